@@ -1,0 +1,327 @@
+"""Benchmark: time to solution of the hyperbolic one-sided block Jacobi method on one GB300.
+
+Workload (one "step" = one full solve through the C ABI): G 512 x 512 Gaussian, J = diag(+1 x 256,
+-1 x 256), block width 32, J_P-sign-pivoted Cholesky (Algorithm 3.3) and the per-cycle
+largest-off-weight ordering, tol = n 2^-53, V accumulated.  Reported metric: matrices/s
+(= 1000 / ms per solve), with the result checked against the tolerances of the test suite.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+N > 1 runs independent replicas (one matrix per rank per step; the method has no exchange on
+one GPU), launched by torch.distributed.run.  --impl reference times the CPU oracle on the
+host cores on the same workload.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N = 512
+BLOCK_W = 32
+EPS = 2.0 ** -53
+METRIC = "time-to-solution and matrices/s at stated eigen rel-error; % FP64/FP32 tensor peak"
+WORKLOAD = "hyperbolic SVD 512x512 Gaussian, J=diag(+1x256,-1x256), w=32, HFSC, per-cycle weight ordering"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--ordering", default="cycle_weight")
+    ap.add_argument("--factor", default="chol_signpiv")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(steps_budget_s=20.0):
+    """The oracle as it stands, 1 host core, full solves of the same workload until ~budget."""
+    import oracle
+    from paper_1008_0201_gb300 import inputs
+
+    G, J = inputs.config2_hyperbolic(n=N)
+    oracle.solve(G[:64, :64], J[:64])  # build + warm
+    times = []
+    t_all = time.perf_counter()
+    while True:
+        t0 = time.perf_counter()
+        r = oracle.solve(G, J)
+        times.append(time.perf_counter() - t0)
+        if time.perf_counter() - t_all > steps_budget_s or len(times) >= 5:
+            break
+    mean = sum(times) / len(times)
+    return {"value": 1.0 / mean, "unit": "matrices/s", "cores": 1, "kind": "oracle",
+            "sample": "%d full solves of the 512x512 hyperbolic problem (row-cyclic pointwise one-sided "
+                      "Jacobi, %d sweeps), %.2f s each" % (len(times), r["sweeps"], mean)}
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_1008_0201_gb300 import inputs
+
+    G, J = inputs.config2_hyperbolic(n=N)
+    for _ in range(args.warmup):
+        oracle.solve(G[:128, :128], J[:128])  # bounded warm-up sample
+    t0 = time.perf_counter()
+    sweeps = 0
+    for _ in range(args.steps):
+        r = oracle.solve(G, J)
+        sweeps = r["sweeps"]
+    dt = (time.perf_counter() - t0) / args.steps
+    val = 1.0 / dt
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "matrices/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD.replace("HFSC, per-cycle weight ordering",
+                                                    "row-cyclic pointwise oracle"), "n": N},
+            "cpu_baseline": {"value": val, "unit": "matrices/s", "cores": 1, "kind": "oracle",
+                             "sample": "each step one full solve (%d sweeps); warm-up on 128x128" % sweeps},
+            "e2e": {"value": val, "unit": "matrices/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return reference_arm(args, rank, world)
+
+    import torch
+
+    import __graft_entry__
+    from paper_1008_0201_gb300 import binding, inputs
+
+    if rank == 0:
+        __graft_entry__.build()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+        dist.barrier()
+        if rank != 0:
+            __graft_entry__.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    lib = binding.load_library()
+
+    G, J = inputs.config2_hyperbolic(n=N, salt=rank)
+    m, n = G.shape
+    opts = binding.default_opts(block_w=BLOCK_W, ordering=args.ordering, factor=args.factor)
+    stream = torch.cuda.current_stream(dev)
+    sptr = stream.cuda_stream
+    # inputs resident in HBM: one fresh column-major copy per step (G is overwritten in place)
+    Gcol = torch.from_numpy(np.ascontiguousarray(G.T)).to(dev)
+    total = args.warmup + args.steps
+    Gs = [Gcol.clone() for _ in range(total)]
+    Jd = torch.from_numpy(J).to(dev)
+    lam = torch.empty(n, dtype=torch.float64, device=dev)
+    U = torch.empty((n, m), dtype=torch.float64, device=dev)
+    V = torch.empty((n, n), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
+
+    def solve(Gbuf):
+        rc, info = binding.jacobi_hsvd_raw(m, n, Gbuf.data_ptr(), m, Jd.data_ptr(), opts, lam.data_ptr(),
+                                           U.data_ptr(), m, V.data_ptr(), n, sptr)
+        if rc != 0:
+            raise RuntimeError("jacobi_hsvd failed: %d %s" % (rc, binding.status_string(rc)))
+        return info
+
+    for i in range(args.warmup):
+        solve(Gs[i])
+    torch.cuda.synchronize()
+
+    # --- timed region: device time of K solves (L2 flushed before each, outside the events)
+    binding.jacobi_profile_begin(("gram", "pivot", "update"))
+    sampler = ClockSampler(local)
+    sampler.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    evs = []
+    infos = []
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        infos.append(solve(Gs[args.warmup + i]))
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    prof = {k: binding.jacobi_profile_read(k) for k in ("gram", "pivot", "update")}
+    binding.jacobi_profile_end()
+    ms = float(np.mean(step_ms))
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    import oracle
+
+    # --- end to end through the C ABI with host buffers: pinned G in, lambda and V out
+    Gh = torch.from_numpy(np.ascontiguousarray(G.T)).pin_memory()
+    lam_h = torch.empty(n, dtype=torch.float64).pin_memory()
+    V_h = torch.empty((n, n), dtype=torch.float64).pin_memory()
+    Gdev = torch.empty_like(Gcol)
+    e2e_ms = []
+    for i in range(max(3, args.steps // 2)):
+        flush.fill_(float(i))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        Gdev.copy_(Gh, non_blocking=True)
+        solve(Gdev)
+        lam_h.copy_(lam, non_blocking=True)
+        V_h.copy_(V, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms.append(e0.elapsed_time(e1))
+    e2e = float(np.mean(e2e_ms))
+    if dist:
+        t = torch.tensor([e2e], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e = float(t.item())
+
+    if rank == 0:
+        info = infos[-1]
+        lam_np = lam_h.numpy().copy()
+        Vn = V_h.numpy().T.copy()
+        ref = oracle.solve(G, J)
+        B = G / np.linalg.norm(G, axis=0)
+        kap = np.linalg.cond(B) ** 2
+        eig_rel = float(np.max(np.abs(lam_np - ref["lam"]) / np.abs(ref["lam"])))
+        J_out = np.where(lam_np < 0, -1, 1).astype(np.int8)
+        vjv = oracle.check_vjv(Vn, J, J_out)
+        ok = eig_rel <= 50 * n * EPS * kap and vjv <= 100 * n * EPS
+        # roofline of the dominant kernel (largest share of the measured kernel time)
+        shares = {k: v[0] for k, v in prof.items()}
+        dom = max(shares, key=shares.get)
+        d_ms, d_n = prof[dom]
+        avg_s = d_ms / max(d_n, 1) * 1e-3
+        steps_per_solve = info["steps_per_sweep"] * info["sweeps"]
+        half = (2 * ((n + 2 * BLOCK_W - 1) // (2 * BLOCK_W))) // 2
+        k = 2 * BLOCK_W
+        if dom == "pivot":
+            # FP32 inner rotations: 3 dot products (6k flops) + F and W column updates (12k flops)
+            rot_per_launch = sum(x["rotations"] for x in infos) / max(1, d_n)
+            flops = rot_per_launch * 18 * k
+            fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12  # unit counts x max SM clock
+            roof = {"bound": "alu", "achieved": flops / avg_s / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
+                    "frac": flops / avg_s / 1e12 / fp32_peak, "traffic": None,
+                    "kernel": "k_pivot", "peak_source": "FP32 lanes x max clock (152 x 128 x 2 x 2.07 GHz)"}
+        else:
+            # FP64 mma: gram m k^2, update (m + n) k^2 multiply-adds per pair
+            macs = half * (m * k * k if dom == "gram" else (m + n) * k * k)
+            fp64_mma_peak = 4.18  # measured mma.sync m16n8k16 f64 throughput, TFLOP/s
+            roof = {"bound": "tensor", "achieved": 2 * macs / avg_s / 1e12, "peak": fp64_mma_peak,
+                    "unit": "TFLOP/s", "frac": 2 * macs / avg_s / 1e12 / fp64_mma_peak, "traffic": None,
+                    "kernel": "k_" + dom, "peak_source": "measured FP64 mma.sync m16n8k16 throughput"}
+        roof["kernel_ms_avg"] = avg_s * 1e3
+        roof["kernel_shares"] = {k2: v / max(sum(shares.values()), 1e-30) for k2, v in shares.items()}
+        line = {
+            "metric": METRIC, "value": world * 1000.0 / ms, "unit": "matrices/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": n, "block_w": BLOCK_W, "ordering": args.ordering,
+                       "factor": args.factor, "sweeps": info["sweeps"], "steps_per_sweep": info["steps_per_sweep"],
+                       "l2": "256 MiB buffer written before each solve, outside the per-solve CUDA events",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "e2e": {"value": world * 1000.0 / e2e, "unit": "matrices/s",
+                    "h2d_bytes_per_step": int(Gh.numel() * 8), "d2h_bytes_per_step": int((n + n * n) * 8)},
+            "gpu_launches": int(sum(x["launches"] for x in infos)),
+            "roofline": roof,
+            "accuracy": {"eig_rel_err": eig_rel, "eig_bound": 50 * n * EPS * kap, "vjv": vjv,
+                         "vjv_bound": 100 * n * EPS, "ok": bool(ok), "max_scaled_off": info["max_scaled_off"]},
+            "clocks": clocks,
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(line))
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

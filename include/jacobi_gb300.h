@@ -1,0 +1,183 @@
+/*
+ * jacobi_gb300.h -- C ABI of the GB300 (sm_103a) block one-sided Jacobi library.
+ *
+ * The library computes the eigendecomposition of a Hermitian matrix given by a factor,
+ *     H = G J G^*,   G: m x n,   J = diag(j_1..j_n), j_k in {+1, -1},
+ * by the parallel one-sided block Jacobi method of Singer, Singer, Novakovic, Uscumlic and
+ * Dunjko, "Novel Modifications of Parallel Jacobi Algorithms":
+ *   - J = I: the one-sided trigonometric algorithm (Sec. 2.1, Sec. 3.1; H positive definite),
+ *   - J != I: the one-sided hyperbolic algorithm, i.e. the hyperbolic SVD G = U Sigma V^{-1}
+ *     with V^* J V = J (Sec. 1, Eq. (1.3); Sec. 3.2, Algorithm 3.4).
+ * G is right-multiplied by J-unitary block transforms V_P (Sec. 2.3) over disjoint pairs of
+ * column blocks chosen by a parallel ordering (Sec. 2.4) until its columns are orthogonal.
+ * Then lambda_k = j_k ||g_k||^2 and u_k = g_k / ||g_k|| (Sec. 3.2).
+ *
+ * Conventions common to every entry point:
+ *   - Matrices are column-major with a leading dimension (ld >= rows).  Real data is IEEE
+ *     double; complex data (dtype JAC_C128) is interleaved (re, im) double pairs and leading
+ *     dimensions count complex elements.
+ *   - Array arguments (G, J, lambda, U, V, ...) are DEVICE pointers on the current CUDA
+ *     device, owned by the caller.  opts and info are HOST pointers.
+ *   - All work is ordered on `stream` (NULL = the legacy default stream).  Each call returns
+ *     after the solve has finished: the sweep loop reads one small convergence record back
+ *     per sweep.  Internal scratch is taken from the stream-ordered allocator
+ *     (cudaMallocAsync) and returned before the call returns.
+ *   - Errors are reported by the return value and never by abort or trap.  A negative value
+ *     -k means argument k (1-based) is invalid; nothing has been written then.  Positive
+ *     values are the jac_status codes below; outputs are then unspecified except for info.
+ *   - Outputs are returned in ascending lambda order; ties keep the input column order.
+ */
+#ifndef JACOBI_GB300_H
+#define JACOBI_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A cudaStream_t (the runtime's stream handle); NULL selects the legacy default stream. */
+typedef struct CUstream_st* jac_stream_t;
+
+/* Return codes (>= 0).  -k: argument k invalid. */
+enum jac_status {
+  JAC_OK = 0,
+  JAC_ENOTCONV = 1,   /* max_sweeps reached with rotations still applied in the last sweep */
+  JAC_ENOTPD = 2,     /* a pivot block G_P^* G_P was not positive definite in its Cholesky
+                         factorization: G lacks full column rank (Sec. 3.2 requires it) */
+  JAC_ENONFINITE = 3, /* G holds a NaN or Inf */
+  JAC_ECUDA = 4,      /* a CUDA runtime call failed */
+  JAC_ENOMEM = 5,     /* device scratch could not be allocated */
+  JAC_EINTERNAL = 6   /* a bounded device loop hit its limit (reported, never trapped) */
+};
+
+/* Element type of G, U, V. */
+enum jac_dtype { JAC_R64 = 0, JAC_C128 = 1 };
+
+/* Parallel block ordering (Sec. 2.4). */
+enum jac_ordering {
+  JAC_ORDER_MODULUS = 0,      /* step k pairs the blocks {p<q: p+q = k mod nb}, nb steps */
+  JAC_ORDER_MODULUS_MOD = 1,  /* modulus, plus the two left-over blocks on even steps */
+  JAC_ORDER_ROUND_ROBIN = 2,  /* circle method: nb-1 perfect matchings */
+  JAC_ORDER_CYCLE_WEIGHT = 3  /* per cycle: pairs by descending ||G_p^* G_q||_F^2 /
+                                 (||G_p||_F^2 ||G_q||_F^2), greedily packed into steps;
+                                 every pair once per cycle */
+};
+
+/* Pivot block processing (Sec. 2.2). */
+enum jac_block_mode { JAC_BLOCK_FULL = 0 /* diagonalize each pivot block (HF/HFSC, TF) */ };
+
+/* Factorization of the pivot block A_P = G_P^* G_P (Sec. 3.2). */
+enum jac_factor {
+  JAC_FACTOR_CHOL = 0,        /* unpivoted Cholesky (HF) */
+  JAC_FACTOR_CHOL_SIGNPIV = 2 /* J_P-sign-pivoted Cholesky, Algorithm 3.3 (HFSC) */
+};
+
+/* Arithmetic of the sweep (all modes return FP64-accurate results). */
+enum jac_precision {
+  JAC_PREC_FP64 = 0 /* Gram / update / J-orthogonalization in FP64 (mma f64) */
+};
+
+typedef struct {
+  int block_w;     /* target block-column width w; nb = max(2, 2*ceil(n/(2w))) blocks whose
+                      widths differ by at most one (Sec. 3).  1 <= w <= 32 in this version. */
+  int ordering;    /* enum jac_ordering */
+  int block_mode;  /* enum jac_block_mode */
+  int factor;      /* enum jac_factor */
+  int precision;   /* enum jac_precision */
+  int max_sweeps;  /* >= 1 */
+  int want_v;      /* 1: accumulate and return V (n x n); 0: V is not touched */
+  double tol;      /* rotate a pair (i,j) iff |a_ij| > tol sqrt(a_ii a_jj); <= 0 selects n*2^-53 */
+} jac_opts;
+
+typedef struct {
+  int sweeps;              /* sweeps run (the last one applied no rotation when converged) */
+  int converged;           /* 1 iff a sweep ended with no rotation */
+  int status;              /* same as the return value */
+  int steps_per_sweep;     /* parallel steps in the last sweep */
+  long long rotations;     /* inner 2x2 rotations applied, all sweeps */
+  long long pivots_rotated;/* pivot blocks transformed, all sweeps */
+  double max_scaled_off;   /* last sweep: max |a_ij| / sqrt(a_ii a_jj) over all pairs seen */
+  double off_rel;          /* last sweep: off_F(G^* G) / ||G||_F^2 estimated from the pivots */
+  long long launches;      /* kernels launched by this call */
+} jac_info;
+
+/* Fills *opts with the defaults: w = 32, round-robin, full block, sign-pivoted Cholesky,
+ * FP64, max_sweeps = 50, want_v = 1, tol = n*2^-53 (tol <= 0). */
+void jacobi_default_opts(jac_opts* opts);
+
+/* Short text for a return code. */
+const char* jacobi_status_string(int status);
+
+/* Library version, major*10000 + minor*100 + patch. */
+int jacobi_version(void);
+
+/*
+ * jacobi_hsvd -- hyperbolic (or, for J = I, trigonometric) one-sided block Jacobi on G.
+ * Sec. 3.2, Algorithm 3.4 (full block; Cholesky per opts->factor, Algorithm 3.3).
+ *
+ *  1 m, 2 n        G is m x n, m >= n >= 1 (full column rank required when J != I).
+ *  3 dtype         JAC_R64 or JAC_C128.
+ *  4 G, 5 ldg      device, in/out.  On return G = G_in V: the unnormalized U Sigma, columns in
+ *                  output order.
+ *  6 J             device int8[n], entries +1 / -1, any order (sorted internally to
+ *                  diag(I, -I) as Sec. 3 assumes; the output order undoes it).
+ *  7 opts          host; NULL selects jacobi_default_opts.
+ *  8 lambda        device double[n]: lambda_k = j_k ||g_k||^2, ascending.
+ *  9 U, 10 ldu     device m x n or NULL: normalized columns g_k/||g_k|| (must not alias G).
+ * 11 V, 12 ldv     device n x n or NULL (required iff opts->want_v): the J-unitary
+ *                  V with G_out = G_in V, V^* J V = J_out (J_out: signs in output order).
+ * 13 info          host, may be NULL.
+ * 14 stream        CUDA stream.
+ */
+int jacobi_hsvd(int m, int n, int dtype, void* G, int ldg, const int8_t* J, const jac_opts* opts,
+                double* lambda, void* U, int ldu, void* V, int ldv, jac_info* info,
+                jac_stream_t stream);
+
+/*
+ * jacobi_eig_pd -- positive definite H = G G^*: jacobi_hsvd with J = I, so only trigonometric
+ * rotations (Eq. (2.1)) are used.  Arguments as jacobi_hsvd without J (positions shift by one:
+ * 1 m, 2 n, 3 dtype, 4 G, 5 ldg, 6 opts, 7 lambda, 8 U, 9 ldu, 10 V, 11 ldv, 12 info,
+ * 13 stream).
+ */
+int jacobi_eig_pd(int m, int n, int dtype, void* G, int ldg, const jac_opts* opts, double* lambda,
+                  void* U, int ldu, void* V, int ldv, jac_info* info, jac_stream_t stream);
+
+/*
+ * jacobi_sched_pairs -- the device scheduler on its own (Sec. 2.4), for inspection and tests.
+ * Writes the block pairs of every step of one cycle for nb blocks (nb even, 2 <= nb <= 4096).
+ *  1 nb
+ *  2 ordering      enum jac_ordering
+ *  3 weights       device double[nb*nb] (row p, column q, q > p used) for
+ *                  JAC_ORDER_CYCLE_WEIGHT, else ignored (may be NULL)
+ *  4 pairs         device int[max_steps * (nb/2) * 2]: pairs[(s*(nb/2) + slot)*2 + {0,1}],
+ *                  p < q; unused slots are set to -1
+ *  5 counts        device int[max_steps]: pairs in step s
+ *  6 max_steps     capacity of pairs/counts in steps (nb for the modulus orderings, nb-1 for
+ *                  round-robin, nb*(nb-1)/2 always suffices for the weight ordering)
+ *  7 nsteps        host int*: number of steps written
+ *  8 stream
+ */
+int jacobi_sched_pairs(int nb, int ordering, const double* weights, int* pairs, int* counts,
+                       int max_steps, int* nsteps, jac_stream_t stream);
+
+/* Kernels that the timing hooks below can bracket. */
+enum jac_kernel { JAC_KERNEL_GRAM = 0, JAC_KERNEL_PIVOT = 1, JAC_KERNEL_UPDATE = 2, JAC_KERNEL_COUNT = 3 };
+
+/*
+ * Kernel timing for measurement tools (no counterpart in the paper).  jacobi_profile_begin(mask)
+ * resets the totals and, until jacobi_profile_end(), brackets every launch of each kernel whose
+ * bit (1 << jac_kernel) is set in mask with a pair of CUDA events on the solve's stream; the
+ * elapsed times are added up when each solve finishes.  jacobi_profile_read returns the total
+ * milliseconds and the number of launches of one kernel.  Host-only state, one process-wide
+ * profile; returns 0 or -k for a bad argument k.
+ */
+int jacobi_profile_begin(int mask);
+int jacobi_profile_read(int kernel, double* total_ms, long long* launches);
+int jacobi_profile_end(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* JACOBI_GB300_H */

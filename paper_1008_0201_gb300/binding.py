@@ -1,0 +1,213 @@
+"""Thin ctypes binding of libjacobi_gb300.so (include/jacobi_gb300.h).
+
+Argument marshalling only: output tensors are allocated with PyTorch on the input's device,
+pointers and the current CUDA stream are passed to the C entry points of the same names, and
+every step of the method runs in the library's kernels.  There is no CPU fallback: if the
+library is missing or the tensors are not on a CUDA device, the calls raise.
+"""
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libjacobi_gb300.so")
+
+JAC_OK, JAC_ENOTCONV, JAC_ENOTPD, JAC_ENONFINITE, JAC_ECUDA, JAC_ENOMEM, JAC_EINTERNAL = range(7)
+JAC_R64, JAC_C128 = 0, 1
+ORDER = {"modulus": 0, "modulus_mod": 1, "round_robin": 2, "cycle_weight": 3}
+FACTOR = {"chol": 0, "chol_signpiv": 2}
+PRECISION = {"fp64": 0}
+
+
+class JacOpts(ctypes.Structure):
+    _fields_ = [("block_w", ctypes.c_int), ("ordering", ctypes.c_int), ("block_mode", ctypes.c_int),
+                ("factor", ctypes.c_int), ("precision", ctypes.c_int), ("max_sweeps", ctypes.c_int),
+                ("want_v", ctypes.c_int), ("tol", ctypes.c_double)]
+
+
+class JacInfo(ctypes.Structure):
+    _fields_ = [("sweeps", ctypes.c_int), ("converged", ctypes.c_int), ("status", ctypes.c_int),
+                ("steps_per_sweep", ctypes.c_int), ("rotations", ctypes.c_longlong),
+                ("pivots_rotated", ctypes.c_longlong), ("max_scaled_off", ctypes.c_double),
+                ("off_rel", ctypes.c_double), ("launches", ctypes.c_longlong)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class JacobiError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (status %d)" % (msg, code))
+        self.code = code
+
+
+_lib = None
+
+EXPORTS = ("jacobi_default_opts", "jacobi_status_string", "jacobi_version", "jacobi_hsvd", "jacobi_eig_pd",
+           "jacobi_sched_pairs", "jacobi_profile_begin", "jacobi_profile_read", "jacobi_profile_end")
+KERNEL = {"gram": 0, "pivot": 1, "update": 2}
+
+
+def load_library(path=LIB_PATH):
+    """dlopen the library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError("libjacobi_gb300.so not found at %s; build it with "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`" % path)
+    lib = ctypes.CDLL(path)
+    P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    lib.jacobi_default_opts.argtypes = [ctypes.POINTER(JacOpts)]
+    lib.jacobi_default_opts.restype = None
+    lib.jacobi_status_string.argtypes = [I]
+    lib.jacobi_status_string.restype = ctypes.c_char_p
+    lib.jacobi_version.argtypes = []
+    lib.jacobi_version.restype = I
+    lib.jacobi_hsvd.argtypes = [I, I, I, P, I, P, ctypes.POINTER(JacOpts), P, P, I, P, I, ctypes.POINTER(JacInfo), P]
+    lib.jacobi_hsvd.restype = I
+    lib.jacobi_eig_pd.argtypes = [I, I, I, P, I, ctypes.POINTER(JacOpts), P, P, I, P, I, ctypes.POINTER(JacInfo), P]
+    lib.jacobi_eig_pd.restype = I
+    lib.jacobi_sched_pairs.argtypes = [I, I, P, P, P, I, ctypes.POINTER(ctypes.c_int), P]
+    lib.jacobi_sched_pairs.restype = I
+    lib.jacobi_profile_begin.argtypes = [I]
+    lib.jacobi_profile_begin.restype = I
+    lib.jacobi_profile_read.argtypes = [I, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong)]
+    lib.jacobi_profile_read.restype = I
+    lib.jacobi_profile_end.argtypes = []
+    lib.jacobi_profile_end.restype = I
+    _lib = lib
+    return lib
+
+
+def default_opts(**kw):
+    lib = load_library()
+    o = JacOpts()
+    lib.jacobi_default_opts(ctypes.byref(o))
+    for key, val in kw.items():
+        if key == "ordering" and isinstance(val, str):
+            val = ORDER[val]
+        elif key == "factor" and isinstance(val, str):
+            val = FACTOR[val]
+        elif key == "precision" and isinstance(val, str):
+            val = PRECISION[val]
+        setattr(o, key, val)
+    return o
+
+
+def status_string(code):
+    return load_library().jacobi_status_string(int(code)).decode()
+
+
+def _stream(dev):
+    return ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+
+
+def _check_cuda(t, name):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % name)
+
+
+def _colmajor(G):
+    """Column-major (Fortran-order) float64 view/copy of a 2-D tensor, as the C ABI expects."""
+    Gt = G.to(torch.float64).t().contiguous()  # (n, m) row-major == (m, n) column-major
+    return Gt
+
+
+def _call(fn_name, G, J, opts, want_u, raise_on_error):
+    lib = load_library()
+    _check_cuda(G, "G")
+    m, n = G.shape
+    dev = G.device
+    Gt = _colmajor(G)  # storage: column c at Gt[c]
+    if opts is None:
+        opts = default_opts()
+    lam = torch.empty(n, dtype=torch.float64, device=dev)
+    Ut = torch.empty((n, m), dtype=torch.float64, device=dev) if want_u else None
+    Vt = torch.empty((n, n), dtype=torch.float64, device=dev) if opts.want_v else None
+    info = JacInfo()
+    args = [m, n, JAC_R64, ctypes.c_void_p(Gt.data_ptr()), m]
+    if fn_name == "jacobi_hsvd":
+        _check_cuda(J, "J")
+        Jd = J.to(device=dev, dtype=torch.int8).contiguous()
+        args.append(ctypes.c_void_p(Jd.data_ptr()))
+    args += [ctypes.byref(opts), ctypes.c_void_p(lam.data_ptr()),
+             ctypes.c_void_p(Ut.data_ptr()) if Ut is not None else None, m,
+             ctypes.c_void_p(Vt.data_ptr()) if Vt is not None else None, n, ctypes.byref(info), _stream(dev)]
+    rc = getattr(lib, fn_name)(*args)
+    if rc != JAC_OK and raise_on_error and not (rc == JAC_ENOTCONV and raise_on_error == "allow_notconv"):
+        raise JacobiError(rc, status_string(rc))
+    out = dict(lam=lam, G=Gt.t(), U=Ut.t() if Ut is not None else None, V=Vt.t() if Vt is not None else None,
+               info=info.as_dict(), status=rc)
+    return out
+
+
+def jacobi_hsvd(G, J, opts=None, want_u=True, raise_on_error=True):
+    """One-sided hyperbolic block Jacobi (J != I) / trigonometric (J = I) on the factor G of
+    H = G J G^T.  G: (m, n) CUDA tensor (not modified; a column-major copy is solved in place);
+    J: (n,) +-1.  Returns dict(lam ascending, G = G_in V, U normalized, V, info, status)."""
+    return _call("jacobi_hsvd", G, J, opts, want_u, raise_on_error)
+
+
+def jacobi_eig_pd(G, opts=None, want_u=True, raise_on_error=True):
+    """Positive definite H = G G^T: jacobi_hsvd with J = I."""
+    return _call("jacobi_eig_pd", G, None, opts, want_u, raise_on_error)
+
+
+def jacobi_hsvd_raw(m, n, G_ptr, ldg, J_ptr, opts, lam_ptr, U_ptr, ldu, V_ptr, ldv, stream_ptr):
+    """Direct pointer-level call (used by the end-to-end timing path); returns (status, info)."""
+    lib = load_library()
+    info = JacInfo()
+    rc = lib.jacobi_hsvd(m, n, JAC_R64, ctypes.c_void_p(G_ptr), ldg, ctypes.c_void_p(J_ptr), ctypes.byref(opts),
+                         ctypes.c_void_p(lam_ptr), ctypes.c_void_p(U_ptr) if U_ptr else None, ldu,
+                         ctypes.c_void_p(V_ptr) if V_ptr else None, ldv, ctypes.byref(info),
+                         ctypes.c_void_p(stream_ptr))
+    return rc, info.as_dict()
+
+
+def jacobi_sched_pairs(nb, ordering, weights=None, device="cuda", max_steps=None):
+    """Device scheduler: list of (count, 2) int tensors, one per step of a cycle."""
+    lib = load_library()
+    if isinstance(ordering, str):
+        ordering = ORDER[ordering]
+    half = nb // 2
+    if max_steps is None:
+        max_steps = 2 * nb
+    pairs = torch.full((max_steps * half * 2,), -7, dtype=torch.int32, device=device)
+    counts = torch.zeros(max_steps, dtype=torch.int32, device=device)
+    w = None
+    if weights is not None:
+        w = weights.to(device=device, dtype=torch.float64).contiguous()
+    ns = ctypes.c_int(0)
+    rc = lib.jacobi_sched_pairs(nb, ordering, ctypes.c_void_p(w.data_ptr()) if w is not None else None,
+                                ctypes.c_void_p(pairs.data_ptr()), ctypes.c_void_p(counts.data_ptr()), max_steps,
+                                ctypes.byref(ns), _stream(torch.device(device)))
+    if rc != JAC_OK:
+        raise JacobiError(rc, "jacobi_sched_pairs failed")
+    tab = pairs.view(max_steps, half, 2).cpu()
+    cnt = counts.cpu()
+    return [tab[s, : int(cnt[s])].clone() for s in range(ns.value)]
+
+
+def jacobi_profile_begin(kernels=("gram", "pivot", "update")):
+    mask = 0
+    for k in kernels:
+        mask |= 1 << KERNEL[k]
+    rc = load_library().jacobi_profile_begin(mask)
+    if rc != 0:
+        raise JacobiError(rc, "jacobi_profile_begin")
+
+
+def jacobi_profile_read(kernel):
+    """(total milliseconds, launches) of one kernel since jacobi_profile_begin."""
+    ms = ctypes.c_double(0.0)
+    n = ctypes.c_longlong(0)
+    rc = load_library().jacobi_profile_read(KERNEL[kernel], ctypes.byref(ms), ctypes.byref(n))
+    if rc != 0:
+        raise JacobiError(rc, "jacobi_profile_read")
+    return ms.value, n.value
+
+
+def jacobi_profile_end():
+    load_library().jacobi_profile_end()

@@ -1,0 +1,201 @@
+// gram_update.cu -- the two dense contractions of a parallel step (Sec. 2.3):
+//   gram:   A_P = [G_p G_q]^* [G_p G_q]                    (Eq. (3.4))
+//   update: [G_p G_q] <- [G_p G_q] V_P,  [V_p V_q] <- [V_p V_q] V_P   (Algorithm 3.4)
+// Both run on the FP64 tensor path (mma.sync m16n8k16 f64), which on GB300 is ~4x the FP64
+// FFMA rate.  The pairs of a step are disjoint, so every CTA owns its columns and the update
+// is in place.
+#include <cooperative_groups.h>
+
+#include "jacobi_common.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace jac {
+
+// smem row stride of a 64-row column slab: 66 doubles = 528 B keeps the 16-byte fragment
+// loads of the 8 column groups in a warp on distinct bank quads.
+#define GRAM_RS 64
+#define GRAM_LDS (GRAM_RS + 2)
+#define GRAM_LDC (JAC_KMAX + 1)
+
+__device__ __forceinline__ int pair_col(int c, int wp, int op, int oq) { return c < wp ? op + c : oq + (c - wp); }
+
+// Grid: half * CS CTAs, cluster (CS,1,1): the CS CTAs of a cluster share one pair and split
+// its rows; their k x k partial sums are added through distributed shared memory, each CTA
+// reducing and storing 1/CS of the entries.  Output Ap[pair] is KMAX x KMAX (k x k used),
+// symmetric, stored column-major.
+__global__ void __launch_bounds__(128) k_gram(JacStepArgs a, const int* __restrict__ step_pairs,
+                                             const int* __restrict__ step_count, int CS,
+                                             double* __restrict__ Ap) {
+  extern __shared__ __align__(16) double gsm[];
+  double* Xs = gsm;                                  // [KMAX cols][GRAM_LDS rows]
+  double* Cs = gsm + JAC_KMAX * GRAM_LDS;            // [KMAX][GRAM_LDC]
+  cg::cluster_group cluster = cg::this_cluster();
+  const int pair = blockIdx.x / CS;
+  const int crank = (int)cluster.block_rank();
+  if (pair >= *step_count) return;  // uniform over the cluster: no cluster barrier is pending
+  const int p = step_pairs[2 * pair], q = step_pairs[2 * pair + 1];
+  const int op = a.boff[p], wp = a.boff[p + 1] - op, oq = a.boff[q], wq = a.boff[q + 1] - oq;
+  const int k = wp + wq, KP = (k + 15) & ~15;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int nti = KP / 16, ntj = KP / 8, ntiles = nti * ntj;
+  // rows of this CTA
+  const int rpc = ((a.mp / CS + 15) & ~15);
+  const int r_begin = min(a.mp, crank * rpc), r_end = min(a.mp, r_begin + rpc);
+
+  double acc[8][4];
+#pragma unroll
+  for (int u = 0; u < 8; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[u][v] = 0.0;
+
+  for (int r0 = r_begin; r0 < r_end; r0 += GRAM_RS) {
+    const int rs = min(GRAM_RS, r_end - r0);  // multiple of 16
+    __syncthreads();
+    // load the slab: column c rows r0..r0+rs-1 (zero columns k..KP-1)
+    for (int idx = threadIdx.x; idx < KP * (rs / 2); idx += blockDim.x) {
+      const int c = idx / (rs / 2), rr = (idx % (rs / 2)) * 2;
+      double2 v = make_double2(0.0, 0.0);
+      if (c < k) v = __ldg(reinterpret_cast<const double2*>(a.Gw + (size_t)pair_col(c, wp, op, oq) * a.mp + r0 + rr));
+      *reinterpret_cast<double2*>(Xs + c * GRAM_LDS + rr) = v;
+    }
+    __syncthreads();
+    for (int kk = 0; kk < rs; kk += 16) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int tile = warp + 4 * u;
+        if (tile < ntiles) {
+          const int ti = tile / ntj, tj = tile % ntj;
+          double av[8], bv[4];
+          const double* xa0 = Xs + (16 * ti + g) * GRAM_LDS + kk + 4 * t;
+          const double* xa1 = xa0 + 8 * GRAM_LDS;
+          const double* xb = Xs + (8 * tj + g) * GRAM_LDS + kk + 4 * t;
+          double2 a0 = *reinterpret_cast<const double2*>(xa0), a1 = *reinterpret_cast<const double2*>(xa0 + 2);
+          double2 a2 = *reinterpret_cast<const double2*>(xa1), a3 = *reinterpret_cast<const double2*>(xa1 + 2);
+          double2 b0 = *reinterpret_cast<const double2*>(xb), b1 = *reinterpret_cast<const double2*>(xb + 2);
+          // a[i]: row g + 8*(i&1), k = 4t + (i>>1)
+          av[0] = a0.x; av[2] = a0.y; av[4] = a1.x; av[6] = a1.y;
+          av[1] = a2.x; av[3] = a2.y; av[5] = a3.x; av[7] = a3.y;
+          bv[0] = b0.x; bv[1] = b0.y; bv[2] = b1.x; bv[3] = b1.y;
+          dmma16816(acc[u], av, bv);
+        }
+      }
+    }
+  }
+  // partial -> own shared memory
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    const int tile = warp + 4 * u;
+    if (tile < ntiles) {
+      const int ti = tile / ntj, tj = tile % ntj;
+      const int r = 16 * ti + g, c = 8 * tj + 2 * t;
+      Cs[r * GRAM_LDC + c] = acc[u][0];
+      Cs[r * GRAM_LDC + c + 1] = acc[u][1];
+      Cs[(r + 8) * GRAM_LDC + c] = acc[u][2];
+      Cs[(r + 8) * GRAM_LDC + c + 1] = acc[u][3];
+    }
+  }
+  cluster.sync();
+  // reduce entries e in [crank*KP*KP/CS, ...) over the CS partials, fixed order
+  const int tot = k * k;
+  const int per = (tot + CS - 1) / CS;
+  const int e0 = crank * per, e1 = min(tot, e0 + per);
+  double* out = Ap + (size_t)pair * JAC_KMAX * JAC_KMAX;
+  for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+    const int i = e % k, j = e / k;
+    double s = 0.0;
+    for (int rk = 0; rk < CS; ++rk) {
+      const double* rc = cluster.map_shared_rank(Cs, rk);
+      s += rc[i * GRAM_LDC + j];
+    }
+    out[j * JAC_KMAX + i] = s;
+  }
+  cluster.sync();  // keep every partial alive until all remote reads are done
+}
+
+// Grid: (half, nslab); slab y covers 64 rows of Gw (y < gslabs) or of Vw.  128 threads.
+// Y = X V_P with X the slab (64 x k), V_P (k x k) from the pivot kernel; written in place.
+#define UPD_RS 64
+#define UPD_LD (JAC_KMAX + 2)
+__global__ void __launch_bounds__(128) k_update(JacStepArgs a, const int* __restrict__ step_pairs,
+                                               const int* __restrict__ step_count,
+                                               const double* __restrict__ vp, const int* __restrict__ skip,
+                                               int gslabs) {
+  extern __shared__ __align__(16) double usm[];
+  double* Bs = usm;                       // V_P: [col j][UPD_LD] (k index contiguous)
+  double* Xs = usm + JAC_KMAX * UPD_LD;   // X slab row-major: [row][UPD_LD]
+  const int pair = blockIdx.x;
+  if (pair >= *step_count || skip[pair]) return;
+  const int p = step_pairs[2 * pair], q = step_pairs[2 * pair + 1];
+  const int op = a.boff[p], wp = a.boff[p + 1] - op, oq = a.boff[q], wq = a.boff[q + 1] - oq;
+  const int k = wp + wq, KP = (k + 15) & ~15;
+  double* base;
+  int ld, r0, rs;
+  if ((int)blockIdx.y < gslabs) {
+    base = a.Gw;
+    ld = a.mp;
+    r0 = blockIdx.y * UPD_RS;
+    rs = min(UPD_RS, a.mp - r0);
+  } else {
+    base = a.Vw;
+    ld = a.np;
+    r0 = (blockIdx.y - gslabs) * UPD_RS;
+    rs = min(UPD_RS, a.np - r0);
+  }
+  if (rs <= 0) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const double* V = vp + (size_t)pair * JAC_KMAX * JAC_KMAX;
+  for (int idx = threadIdx.x; idx < KP * KP; idx += blockDim.x) {
+    const int c = idx % KP, j = idx / KP;  // V_P[c][j], column-major source
+    Bs[j * UPD_LD + c] = (c < k && j < k) ? V[j * JAC_KMAX + c] : 0.0;
+  }
+  for (int idx = threadIdx.x; idx < KP * rs; idx += blockDim.x) {
+    const int r = idx % rs, c = idx / rs;
+    Xs[r * UPD_LD + c] = (c < k) ? base[(size_t)pair_col(c, wp, op, oq) * ld + r0 + r] : 0.0;
+  }
+  __syncthreads();
+  const int nti = rs / 16, ntj = KP / 8, ntiles = nti * ntj;
+  double acc[8][4];
+#pragma unroll
+  for (int u = 0; u < 8; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[u][v] = 0.0;
+  for (int kk = 0; kk < KP; kk += 16) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int tile = warp + 4 * u;
+      if (tile < ntiles) {
+        const int ti = tile / ntj, tj = tile % ntj;
+        const double* xa0 = Xs + (16 * ti + g) * UPD_LD + kk + 4 * t;
+        const double* xa1 = xa0 + 8 * UPD_LD;
+        const double* xb = Bs + (8 * tj + g) * UPD_LD + kk + 4 * t;
+        double2 a0 = *reinterpret_cast<const double2*>(xa0), a1 = *reinterpret_cast<const double2*>(xa0 + 2);
+        double2 a2 = *reinterpret_cast<const double2*>(xa1), a3 = *reinterpret_cast<const double2*>(xa1 + 2);
+        double2 b0 = *reinterpret_cast<const double2*>(xb), b1 = *reinterpret_cast<const double2*>(xb + 2);
+        double av[8], bv[4];
+        av[0] = a0.x; av[2] = a0.y; av[4] = a1.x; av[6] = a1.y;
+        av[1] = a2.x; av[3] = a2.y; av[5] = a3.x; av[7] = a3.y;
+        bv[0] = b0.x; bv[1] = b0.y; bv[2] = b1.x; bv[3] = b1.y;
+        dmma16816(acc[u], av, bv);
+      }
+    }
+  }
+  __syncthreads();  // all reads of Xs done: reuse it for the result
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    const int tile = warp + 4 * u;
+    if (tile < ntiles) {
+      const int ti = tile / ntj, tj = tile % ntj;
+      const int r = 16 * ti + g, c = 8 * tj + 2 * t;
+      *reinterpret_cast<double2*>(Xs + r * UPD_LD + c) = make_double2(acc[u][0], acc[u][1]);
+      *reinterpret_cast<double2*>(Xs + (r + 8) * UPD_LD + c) = make_double2(acc[u][2], acc[u][3]);
+    }
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < k * rs; idx += blockDim.x) {
+    const int r = idx % rs, c = idx / rs;
+    base[(size_t)pair_col(c, wp, op, oq) * ld + r0 + r] = Xs[r * UPD_LD + c];
+  }
+}
+
+}  // namespace jac

@@ -1,0 +1,107 @@
+// jacobi_common.cuh -- shared device helpers and internal types of the GB300 Jacobi library.
+//
+// Arithmetic placement on GB300 (measured on the target: FP64 FFMA ~1.0 TFLOP/s, mma.sync
+// m16n8k16 f64 ~4.2 TFLOP/s, FP32 FFMA ~74 TFLOP/s, FP64 sqrt/div ~650 cycles latency):
+//   - every FP64 contraction (pivot Gram block, block update, J-orthogonalization of V_P)
+//     runs on the FP64 tensor path, mma.sync.m16n8k16.f64;
+//   - the 2x2 rotation angles are computed in FP32 on a shifted representation that keeps
+//     relative precision near convergence; FP64 enters them only through A_P.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define JAC_KMAX 64          // largest pivot block order k = w_p + w_q handled (w <= 32)
+#define JAC_WMAX 32          // largest block width
+#define JAC_INNER_MAX_SWEEPS 40
+
+// device error flags (OR-ed into a global word; never trapped)
+#define JAC_DEVERR_NOTPD 1u
+#define JAC_DEVERR_INNER_LIMIT 2u
+#define JAC_DEVERR_NONFINITE 4u
+
+namespace jac {
+
+// D = A(16x16) * B(16x8) + C, f64.  Fragment layout (checked on the target against a CPU
+// product): lane = 4g + t; A element (row g + 8*(i&1), k = 4t + (i>>1)) in a[i]; B element
+// (k = 4t + j, col g) in b[j]; C/D element (row g + 8*(i>>1), col 2t + (i&1)) in c[i].
+// Any permutation of k applied to both A and B gives the same product; this one makes the
+// four k-values of a thread contiguous.
+__device__ __forceinline__ void dmma16816(double (&c)[4], const double (&a)[8], const double (&b)[4]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f64.f64.f64.f64 {%0,%1,%2,%3}, "
+      "{%4,%5,%6,%7,%8,%9,%10,%11}, {%12,%13,%14,%15}, {%0,%1,%2,%3};\n"
+      : "+d"(c[0]), "+d"(c[1]), "+d"(c[2]), "+d"(c[3])
+      : "d"(a[0]), "d"(a[1]), "d"(a[2]), "d"(a[3]), "d"(a[4]), "d"(a[5]), "d"(a[6]), "d"(a[7]),
+        "d"(b[0]), "d"(b[1]), "d"(b[2]), "d"(b[3]));
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ double warp_max_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+__device__ __forceinline__ int warp_sum_i(int v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+}  // namespace jac
+
+// ------------------------------------------------------------------ internal problem view
+// Internal layout: Gw is (mp x n) column-major, ld = mp = m rounded up to 16 with zero rows;
+// columns are sorted so that J = diag(I_npos, -I).  Vw is (np x n), np = n rounded up to 16.
+// Block b spans columns [boff[b], boff[b+1]).
+struct JacStepArgs {
+  double* Gw;
+  int mp;            // rows of Gw (multiple of 16), also its ld
+  double* Vw;        // NULL if V is not accumulated
+  int np;            // rows of Vw (multiple of 16), also its ld
+  int n;
+  int nb;
+  const int* boff;   // [nb+1]
+  const int8_t* Js;  // [n] internal (sorted) signs
+  const int* pairs;  // [steps][half][2]
+  const int* counts; // [steps]
+  int half;          // nb/2
+};
+
+struct PivotParams {
+  double tol;        // outer rotation threshold
+  int factor;        // 0 unpivoted, 2 sign-pivoted
+};
+
+// per (step, pair) record written by the pivot kernel, reduced per sweep
+struct PairStat {
+  double max_scaled;  // max |a_ij|/sqrt(a_ii a_jj) over the pivot block
+  double off2_cross;  // sum over the cross block A_pq of |a_ij|^2 (one triangle)
+  double off2_diag;   // sum over the strictly upper parts of A_pp and A_qq of |a_ij|^2
+  double trace;       // sum of a_ii over the pivot block
+  int rotations;      // inner rotations applied (0: the pair was already diagonal)
+  int inner_sweeps;
+  int ns_steps;
+  int active;         // 1 iff some |a_ij| > tol sqrt(a_ii a_jj): the FP64 convergence test
+};
+
+struct SweepRecord {
+  double max_scaled;
+  double off2;
+  double trace;
+  long long rotations;
+  long long pivots_rotated;
+  unsigned int err;
+  int pad;
+};
