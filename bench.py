@@ -30,6 +30,8 @@ BLOCK_W = 32
 EPS = 2.0 ** -53
 METRIC = "time-to-solution and matrices/s at stated eigen rel-error; % FP64/FP32 tensor peak"
 WORKLOAD = "hyperbolic SVD 512x512 Gaussian, J=diag(+1x256,-1x256), w=32, HFSC, per-cycle weight ordering"
+# dtype of the arithmetic: FP64 contractions and FP32 inner rotations; the mixed mode runs its
+# early sweeps on an FP32 copy (FP32 products) before the FP64 polish
 
 
 def parse():
@@ -40,6 +42,7 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--ordering", default="cycle_weight")
     ap.add_argument("--factor", default="chol_signpiv")
+    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -182,7 +185,8 @@ def main():
 
     G, J = inputs.config2_hyperbolic(n=N, salt=rank)
     m, n = G.shape
-    opts = binding.default_opts(block_w=BLOCK_W, ordering=args.ordering, factor=args.factor)
+    opts = binding.default_opts(block_w=BLOCK_W, ordering=args.ordering, factor=args.factor,
+                                precision=args.precision)
     stream = torch.cuda.current_stream(dev)
     sptr = stream.cuda_stream
     # inputs resident in HBM: one fresh column-major copy per step (G is overwritten in place)
@@ -303,7 +307,9 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": n, "block_w": BLOCK_W, "ordering": args.ordering,
-                       "factor": args.factor, "sweeps": info["sweeps"], "steps_per_sweep": info["steps_per_sweep"],
+                       "factor": args.factor, "precision": args.precision, "sweeps": info["sweeps"],
+                       "fp32_sweeps": info["lowp_sweeps"], "steps_per_sweep": info["steps_per_sweep"],
+                       "pivot_phase_share": [c / max(1, sum(info["pivot_cycles"])) for c in info["pivot_cycles"]],
                        "l2": "256 MiB buffer written before each solve, outside the per-solve CUDA events",
                        "parallelism": "replicas" if world > 1 else "single"},
             "e2e": {"value": world * 1000.0 / e2e, "unit": "matrices/s",

@@ -73,9 +73,13 @@ enum jac_factor {
   JAC_FACTOR_CHOL_SIGNPIV = 2 /* J_P-sign-pivoted Cholesky, Algorithm 3.3 (HFSC) */
 };
 
-/* Arithmetic of the sweep (all modes return FP64-accurate results). */
+/* Arithmetic of the sweeps (both modes return FP64-accurate results). */
 enum jac_precision {
-  JAC_PREC_FP64 = 0 /* Gram / update / J-orthogonalization in FP64 (mma f64) */
+  JAC_PREC_FP64 = 0, /* every sweep: Gram, update and J-orthogonalization of V_P in FP64 (mma f64) */
+  JAC_PREC_FP32 = 1  /* sweeps on an FP32 copy of G with FP32 Gram/update products until the scaled
+                        off-norm reaches what FP32 resolves, then V is made J-unitary in FP64,
+                        G = G_in V, and FP64 sweeps polish to tol (the outer iteration is
+                        self-correcting, Sec. 4) */
 };
 
 typedef struct {
@@ -100,6 +104,11 @@ typedef struct {
   double max_scaled_off;   /* last sweep: max |a_ij| / sqrt(a_ii a_jj) over all pairs seen */
   double off_rel;          /* last sweep: off_F(G^* G) / ||G||_F^2 estimated from the pivots */
   long long launches;      /* kernels launched by this call */
+  int lowp_sweeps;         /* sweeps of the FP32 phase (JAC_PREC_FP32) */
+  int global_ns_steps;     /* Newton-Schulz steps applied to the accumulated V after that phase */
+  long long pivot_ns_steps;/* Newton-Schulz steps applied to pivot transforms V_P */
+  long long pivot_cycles[4]; /* SM clocks summed over pivots: statistics, Cholesky, inner sweeps,
+                                J-orthogonalization */
 } jac_info;
 
 /* Fills *opts with the defaults: w = 32, round-robin, full block, sign-pivoted Cholesky,

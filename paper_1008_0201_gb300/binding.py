@@ -17,7 +17,7 @@ JAC_OK, JAC_ENOTCONV, JAC_ENOTPD, JAC_ENONFINITE, JAC_ECUDA, JAC_ENOMEM, JAC_EIN
 JAC_R64, JAC_C128 = 0, 1
 ORDER = {"modulus": 0, "modulus_mod": 1, "round_robin": 2, "cycle_weight": 3}
 FACTOR = {"chol": 0, "chol_signpiv": 2}
-PRECISION = {"fp64": 0}
+PRECISION = {"fp64": 0, "fp32": 1}
 
 
 class JacOpts(ctypes.Structure):
@@ -30,10 +30,15 @@ class JacInfo(ctypes.Structure):
     _fields_ = [("sweeps", ctypes.c_int), ("converged", ctypes.c_int), ("status", ctypes.c_int),
                 ("steps_per_sweep", ctypes.c_int), ("rotations", ctypes.c_longlong),
                 ("pivots_rotated", ctypes.c_longlong), ("max_scaled_off", ctypes.c_double),
-                ("off_rel", ctypes.c_double), ("launches", ctypes.c_longlong)]
+                ("off_rel", ctypes.c_double), ("launches", ctypes.c_longlong), ("lowp_sweeps", ctypes.c_int),
+                ("global_ns_steps", ctypes.c_int), ("pivot_ns_steps", ctypes.c_longlong),
+                ("pivot_cycles", ctypes.c_longlong * 4)]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_}
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f != "pivot_cycles"}
+        d["pivot_cycles"] = list(self.pivot_cycles)
+        return d
+
 
 
 class JacobiError(RuntimeError):

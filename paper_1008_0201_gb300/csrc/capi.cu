@@ -19,7 +19,18 @@ namespace jac {
 __global__ void k_sched_static(int nb, int ordering, int nsteps, int* pairs, int* counts);
 __global__ void k_sched_cycle_weight(int nb, const double* w, int* order_g, int* pairs, int* counts, int max_steps,
                                      int* nsteps_out);
-__global__ void k_block_weights(const double* Gw, int mp, int nb, const int* boff, double* w);
+__global__ void k_block_weights32(const float* G32, int mp, int nb, const int* boff, double* w);
+__global__ void k_gram32(JacStepArgs a, const float* G32, const int* step_pairs, const int* step_count, int CS,
+                         double* Ap);
+__global__ void k_update32(JacStepArgs a, float* G32, float* V32, const int* step_pairs, const int* step_count,
+                           const double* vp, const int* skip, int gslabs);
+__global__ void k_gemm64(int Mr, int Nc, int K, const double* A, int lda, int transA, const double* B, int ldb,
+                         const int8_t* sb, const int8_t* dsub, double* C, int ldc, int sym);
+__global__ void k_ns_correct(int Mr, int Nc, int K, const float* Af, int lda, const float* Bf, int ldb, double* V,
+                             int ldv);
+__global__ void k_cvt64to32(int rows, int cols, const double* src, int lds, float* dst, int ldd, const int8_t* rsign);
+__global__ void k_cvt32to64(int rows, int cols, const float* src, int lds, double* dst, int ldd);
+__global__ void k_absmax64(int n, const double* M, int ldm, unsigned long long* out);
 __global__ void k_gram(JacStepArgs a, const int* step_pairs, const int* step_count, int CS, double* Ap);
 __global__ void k_update(JacStepArgs a, const int* step_pairs, const int* step_count, const double* vp,
                          const int* skip, int gslabs);
@@ -115,10 +126,14 @@ int setup_attributes(int dev) {
     return JAC_ECUDA;
   if (cudaFuncSetAttribute(k_gram, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
     return JAC_ECUDA;
+  if (cudaFuncSetAttribute(k_gram32, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+    return JAC_ECUDA;
   if (cudaFuncSetAttribute(k_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kUpdSmem) != cudaSuccess)
     return JAC_ECUDA;
   if (cudaFuncSetAttribute(k_pivot, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pivot_smem_bytes()) !=
       cudaSuccess)
+    return JAC_ECUDA;
+  if (cudaFuncSetAttribute(k_rank, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024) != cudaSuccess)
     return JAC_ECUDA;
   g_attr_done[dev] = true;
   return 0;
@@ -138,24 +153,33 @@ struct Arena {
 };
 
 struct Layout {
-  double *Gw, *Vw, *Ap, *vp, *weights, *nrm2, *lam;
+  double *Gw, *Vw, *Ap, *vp, *weights, *nrm2, *lam, *Mn;
+  float *G32, *V32, *Mf, *Vf;
   int *boff, *perm_in, *pairs, *counts, *skip, *order, *nsteps, *rank;
-  int8_t* Js;
+  int8_t *Js, *Jin;
   PairStat* stats;
   SweepRecord* rec;
   unsigned* err;
+  unsigned long long* mmax;
 };
 
-size_t carve(Arena& ar, Layout& L, int mp, int np, int n, int nb, int max_steps, bool want_v, bool weights) {
+size_t carve(Arena& ar, Layout& L, int m, int mp, int np, int n, int nb, int max_steps, bool have_vw, bool weights,
+             bool need_g32, bool mixed) {
+  (void)m;
   const int half = nb / 2;
   const int npairs = nb * (nb - 1) / 2;
   L.Gw = ar.take<double>((size_t)mp * n);
-  L.Vw = want_v ? ar.take<double>((size_t)np * n) : nullptr;
+  L.Vw = have_vw ? ar.take<double>((size_t)np * n) : nullptr;
   L.Ap = ar.take<double>((size_t)half * JAC_KMAX * JAC_KMAX);
   L.vp = ar.take<double>((size_t)half * JAC_KMAX * JAC_KMAX);
   L.weights = weights ? ar.take<double>((size_t)nb * nb) : nullptr;
   L.nrm2 = ar.take<double>(n);
   L.lam = ar.take<double>(n);
+  L.Mn = mixed ? ar.take<double>((size_t)n * n) : nullptr;
+  L.G32 = need_g32 ? ar.take<float>((size_t)mp * n) : nullptr;
+  L.V32 = mixed ? ar.take<float>((size_t)np * n) : nullptr;
+  L.Mf = mixed ? ar.take<float>((size_t)n * n) : nullptr;
+  L.Vf = mixed ? ar.take<float>((size_t)n * n) : nullptr;
   L.boff = ar.take<int>(nb + 1);
   L.perm_in = ar.take<int>(n);
   L.pairs = ar.take<int>((size_t)max_steps * half * 2);
@@ -165,9 +189,11 @@ size_t carve(Arena& ar, Layout& L, int mp, int np, int n, int nb, int max_steps,
   L.nsteps = ar.take<int>(1);
   L.rank = ar.take<int>(n);
   L.Js = ar.take<int8_t>(n);
+  L.Jin = ar.take<int8_t>(n);
   L.stats = ar.take<PairStat>((size_t)max_steps * half);
   L.rec = ar.take<SweepRecord>(1);
   L.err = ar.take<unsigned>(1);
+  L.mmax = ar.take<unsigned long long>(1);
   return ar.off;
 }
 
@@ -177,11 +203,12 @@ int choose_cluster(int half, int mp) {
   return cs;
 }
 
-int launch_gram(const JacStepArgs& a, const int* sp, const int* sc, int half, int CS, double* Ap, cudaStream_t st) {
+template <class Kern, class... Args>
+int launch_cluster(Kern kern, int half, int CS, int threads, size_t smem, cudaStream_t st, Args... args) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(half * CS);
-  cfg.blockDim = dim3(128);
-  cfg.dynamicSmemBytes = kGramSmem;
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -190,7 +217,7 @@ int launch_gram(const JacStepArgs& a, const int* sp, const int* sc, int half, in
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_gram, a, sp, sc, CS, Ap) == cudaSuccess ? 0 : JAC_ECUDA;
+  return cudaLaunchKernelEx(&cfg, kern, args...) == cudaSuccess ? 0 : JAC_ECUDA;
 }
 
 // Validates the options; returns 0 or the (negative) argument position of opts.
@@ -199,7 +226,7 @@ int check_opts(const jac_opts& o, int argpos) {
   if (o.ordering < 0 || o.ordering > 3) return -argpos;
   if (o.block_mode != JAC_BLOCK_FULL) return -argpos;
   if (o.factor != JAC_FACTOR_CHOL && o.factor != JAC_FACTOR_CHOL_SIGNPIV) return -argpos;
-  if (o.precision != JAC_PREC_FP64) return -argpos;
+  if (o.precision != JAC_PREC_FP64 && o.precision != JAC_PREC_FP32) return -argpos;
   if (o.max_sweeps < 1) return -argpos;
   if (o.want_v != 0 && o.want_v != 1) return -argpos;
   return 0;
@@ -228,7 +255,7 @@ int solve(int m, int n, int dtype, void* Gv, int ldg, const int8_t* Jdev, const 
     return -pos;
   };
   if (m < 1) return fail_arg(ap.m);
-  if (n < 1 || n > m) return fail_arg(ap.n);
+  if (n < 1 || n > m || n > 20000) return fail_arg(ap.n);
   if (dtype != JAC_R64) return fail_arg(ap.dtype);
   if (!Gv) return fail_arg(ap.G);
   if (ldg < m) return fail_arg(ap.ldg);
@@ -276,12 +303,15 @@ int solve(int m, int n, int dtype, void* Gv, int ldg, const int8_t* Jdev, const 
     boff[nb] = off;
   }
   const bool weights = (o.ordering == JAC_ORDER_CYCLE_WEIGHT);
+  const bool mixed = (o.precision == JAC_PREC_FP32);
   const int max_steps = (o.ordering == JAC_ORDER_ROUND_ROBIN) ? nb - 1 : (weights ? 2 * nb : nb);
   const bool want_v = o.want_v != 0;
+  const bool have_vw = want_v || mixed;  // the mixed mode needs V internally for G = G_in V
+  const bool need_g32 = mixed || weights;
 
   Arena ar;
   Layout L;
-  const size_t bytes = carve(ar, L, mp, np, n, nb, max_steps, want_v, weights);
+  const size_t bytes = carve(ar, L, m, mp, np, n, nb, max_steps, have_vw, weights, need_g32, mixed);
   void* base = nullptr;
   if (cudaMallocAsync(&base, bytes, st) != cudaSuccess) {
     cudaGetLastError();
@@ -289,24 +319,24 @@ int solve(int m, int n, int dtype, void* Gv, int ldg, const int8_t* Jdev, const 
   }
   Arena ar2;
   ar2.base = static_cast<char*>(base);
-  carve(ar2, L, mp, np, n, nb, max_steps, want_v, weights);
+  carve(ar2, L, m, mp, np, n, nb, max_steps, have_vw, weights, need_g32, mixed);
 
   int status = JAC_OK;
   auto ck = [&](cudaError_t e) {
     if (e != cudaSuccess && status == JAC_OK) status = JAC_ECUDA;
   };
-  // small host -> device uploads
-  std::vector<char> up;
   ck(cudaMemcpyAsync(L.boff, boff.data(), sizeof(int) * (nb + 1), cudaMemcpyHostToDevice, st));
   ck(cudaMemcpyAsync(L.perm_in, perm_in.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
   ck(cudaMemcpyAsync(L.Js, Js.data(), n, cudaMemcpyHostToDevice, st));
+  ck(cudaMemcpyAsync(L.Jin, Jh.data(), n, cudaMemcpyHostToDevice, st));
   ck(cudaMemsetAsync(L.err, 0, sizeof(unsigned), st));
 
-  long long launches = want_v ? 3 : 2;
+  long long launches = have_vw ? 3 : 2;
   const double* G = static_cast<const double*>(Gv);
+  const int ew_blocks = std::min(1024, (int)(((size_t)mp * n + 255) / 256));
   k_check_finite<<<std::min(1024, (int)(((size_t)m * n + 255) / 256)), 256, 0, st>>>(G, ldg, m, n, L.err);
   k_gather_in<<<dim3((mp + 255) / 256, n), 256, 0, st>>>(G, ldg, m, mp, L.perm_in, L.Gw);
-  if (want_v) k_init_v<<<dim3((np + 255) / 256, n), 256, 0, st>>>(n, np, L.perm_in, L.Vw);
+  if (have_vw) k_init_v<<<dim3((np + 255) / 256, n), 256, 0, st>>>(n, np, L.perm_in, L.Vw);
   ck(cudaGetLastError());
   unsigned herr = 0;
   ck(cudaMemcpyAsync(&herr, L.err, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
@@ -332,23 +362,40 @@ int solve(int m, int n, int dtype, void* Gv, int ldg, const int8_t* Jdev, const 
   args.pairs = L.pairs;
   args.counts = L.counts;
   args.half = half;
-  PivotParams pp;
-  pp.tol = o.tol;
-  pp.factor = o.factor;
   const int CS = choose_cluster(half, mp);
   const int gslabs = (mp + 63) / 64;
-  const int vslabs = want_v ? (np + 63) / 64 : 0;
+  const int vslabs = have_vw ? (np + 63) / 64 : 0;
+  // FP32 phase: stop at the scaled off-norm the FP32 Gram still resolves (its entries carry
+  // errors ~ eps_32 sqrt(m) relative to ||g_i|| ||g_j||)
+  const double tau_lo = std::max(o.tol, 8.0 * 5.9604644775390625e-08 * std::sqrt((double)m));
+  int phase = mixed ? 1 : 3;
+  if (mixed && status == JAC_OK) {
+    k_cvt64to32<<<ew_blocks, 256, 0, st>>>(mp, n, L.Gw, mp, L.G32, mp, nullptr);
+    k_cvt64to32<<<ew_blocks, 256, 0, st>>>(np, n, L.Vw, np, L.V32, np, nullptr);
+    launches += 2;
+    ck(cudaGetLastError());
+  }
 
-  int sweeps = 0, converged = 0;
-  long long rot_total = 0, piv_total = 0;
-  ProfRun prof;
-  prof.begin();
+  int sweeps = 0, converged = 0, lowp_sweeps = 0, ns_global = 0;
+  long long rot_total = 0, piv_total = 0, cyc_total[4] = {0, 0, 0, 0}, ns_total = 0;
+  double prev_max = 1e300;
   SweepRecord hrec = {};
   int last_steps = 0;
+  ProfRun prof;
+  prof.begin();
   for (int sw = 0; status == JAC_OK && n > 1 && sw < o.max_sweeps; ++sw) {
+    const bool low = (phase == 1);
+    PivotParams pp;
+    pp.tol = low ? tau_lo : o.tol;
+    pp.factor = o.factor;
+    pp.ns_mode = low ? 0 : 1;
     if (weights) {
       const int npairs = nb * (nb - 1) / 2;
-      k_block_weights<<<npairs, 128, 0, st>>>(L.Gw, mp, nb, L.boff, L.weights);
+      if (!low) {
+        k_cvt64to32<<<ew_blocks, 256, 0, st>>>(mp, n, L.Gw, mp, L.G32, mp, nullptr);
+        ++launches;
+      }
+      k_block_weights32<<<npairs, 256, 0, st>>>(L.G32, mp, nb, L.boff, L.weights);
       k_sched_cycle_weight<<<1, 1024, sizeof(int) * nb, st>>>(nb, L.weights, L.order, L.pairs, L.counts,
                                                               max_steps, L.nsteps);
       launches += 2;
@@ -365,14 +412,23 @@ int solve(int m, int n, int dtype, void* Gv, int ldg, const int8_t* Jdev, const 
       const int* sp = L.pairs + (size_t)s * half * 2;
       const int* sc = L.counts + s;
       size_t pm = prof.pre(JAC_KERNEL_GRAM, st);
-      if (int r = launch_gram(args, sp, sc, half, CS, L.Ap, st)) status = r;
+      if (low) {
+        if (int r = launch_cluster(k_gram32, half, CS, 128, 0, st, args, (const float*)L.G32, sp, sc, CS, L.Ap))
+          status = r;
+      } else {
+        if (int r = launch_cluster(k_gram, half, CS, 128, kGramSmem, st, args, sp, sc, CS, L.Ap)) status = r;
+      }
       prof.post(pm, st);
       pm = prof.pre(JAC_KERNEL_PIVOT, st);
       k_pivot<<<half, 1024, pivot_smem_bytes(), st>>>(args, sp, sc, L.Ap, pp, L.vp, L.skip,
                                                       L.stats + (size_t)s * half, L.err);
       prof.post(pm, st);
       pm = prof.pre(JAC_KERNEL_UPDATE, st);
-      k_update<<<dim3(half, gslabs + vslabs), 128, kUpdSmem, st>>>(args, sp, sc, L.vp, L.skip, gslabs);
+      if (low) {
+        k_update32<<<dim3(half, gslabs + vslabs), 256, 0, st>>>(args, L.G32, L.V32, sp, sc, L.vp, L.skip, gslabs);
+      } else {
+        k_update<<<dim3(half, gslabs + vslabs), 128, kUpdSmem, st>>>(args, sp, sc, L.vp, L.skip, gslabs);
+      }
       prof.post(pm, st);
       launches += 3;
       ck(cudaGetLastError());
@@ -387,9 +443,56 @@ int solve(int m, int n, int dtype, void* Gv, int ldg, const int8_t* Jdev, const 
     last_steps = nsteps;
     rot_total += hrec.rotations;
     piv_total += hrec.pivots_rotated;
+    ns_total += hrec.ns_steps;
+    for (int u = 0; u < 4; ++u) cyc_total[u] += hrec.cyc[u];
     if (hrec.err & JAC_DEVERR_NOTPD) {
       status = JAC_ENOTPD;
       break;
+    }
+    if (low) {
+      ++lowp_sweeps;
+      // leave the FP32 phase when it has converged at tau_lo, when the off-norm stalls, or
+      // when only the sweeps the polish needs are left
+      const bool stalled = hrec.max_scaled < 1e-3 && hrec.max_scaled > 0.5 * prev_max;
+      const bool done = hrec.pivots_rotated == 0 || stalled || sw + 4 >= o.max_sweeps;
+      prev_max = hrec.max_scaled;
+      if (done) {
+        // phase 2: V (FP32) -> FP64, J-unitary by Newton-Schulz, then G = G_in V
+        k_cvt32to64<<<ew_blocks, 256, 0, st>>>(np, n, L.V32, np, L.Vw, np);
+        launches += 1;
+        const dim3 gsym((n + 31) / 32, (n + 31) / 32);
+        for (int it = 0; it < 4 && status == JAC_OK; ++it) {
+          k_gemm64<<<gsym, 128, 0, st>>>(n, n, n, L.Vw, np, 1, L.Vw, np, L.Jin, L.Js, L.Mn, n, 1);
+          ck(cudaMemsetAsync(L.mmax, 0, sizeof(unsigned long long), st));
+          k_absmax64<<<std::min(1024, (n * n + 255) / 256), 256, 0, st>>>(n, L.Mn, n, L.mmax);
+          unsigned long long hm = 0;
+          ck(cudaMemcpyAsync(&hm, L.mmax, sizeof(hm), cudaMemcpyDeviceToHost, st));
+          ck(cudaStreamSynchronize(st));
+          launches += 2;
+          double mm;
+          std::memcpy(&mm, &hm, sizeof(mm));
+          if (!(mm == mm) || mm > 0.25) {  // V32 too far from J-unitary to correct
+            status = JAC_EINTERNAL;
+            break;
+          }
+          if (mm <= 4e-16) break;
+          // V <- V - V (J_c M) / 2, the correction in FP32
+          k_cvt64to32<<<ew_blocks, 256, 0, st>>>(n, n, L.Mn, n, L.Mf, n, L.Js);
+          k_cvt64to32<<<ew_blocks, 256, 0, st>>>(n, n, L.Vw, np, L.Vf, n, nullptr);
+          k_ns_correct<<<dim3((n + 63) / 64, (n + 63) / 64), 256, 0, st>>>(n, n, n, L.Vf, n, L.Mf, n, L.Vw, np);
+          launches += 3;
+          ++ns_global;
+          ck(cudaGetLastError());
+          if (mm * mm + 1e-6 * mm <= 2e-16) break;
+        }
+        // G_int = G_in V (V rows are input columns): the FP64 factor the polish works on
+        k_gemm64<<<dim3((m + 31) / 32, (n + 31) / 32), 128, 0, st>>>(m, n, n, G, ldg, 0, L.Vw, np, nullptr,
+                                                                     nullptr, L.Gw, mp, 0);
+        ++launches;
+        ck(cudaGetLastError());
+        phase = 3;
+      }
+      continue;
     }
     if (hrec.pivots_rotated == 0) {
       converged = 1;
@@ -401,7 +504,7 @@ int solve(int m, int n, int dtype, void* Gv, int ldg, const int8_t* Jdev, const 
 
   if (status == JAC_OK || status == JAC_ENOTCONV) {
     k_colnorm<<<(n * 32 + 255) / 256, 256, 0, st>>>(L.Gw, mp, n, L.Js, L.nrm2, L.lam);
-    k_rank<<<(n + 255) / 256, 256, 0, st>>>(L.lam, n, L.rank);
+    k_rank<<<(n + 255) / 256, 256, sizeof(unsigned long long) * n, st>>>(L.lam, n, L.rank);
     k_scatter<<<n, 128, 0, st>>>(L.Gw, mp, m, L.Vw, np, n, L.nrm2, L.lam, L.rank, lambda, static_cast<double*>(Gv),
                                  ldg, static_cast<double*>(Uv), ldu, want_v ? static_cast<double*>(Vv) : nullptr,
                                  ldv);
@@ -421,6 +524,10 @@ int solve(int m, int n, int dtype, void* Gv, int ldg, const int8_t* Jdev, const 
     info->max_scaled_off = hrec.max_scaled;
     info->off_rel = (hrec.trace > 0.0) ? std::sqrt(hrec.off2) / hrec.trace : 0.0;
     info->launches = launches;
+    info->lowp_sweeps = lowp_sweeps;
+    info->global_ns_steps = ns_global;
+    info->pivot_ns_steps = ns_total;
+    for (int u = 0; u < 4; ++u) info->pivot_cycles[u] = cyc_total[u];
   }
   return status;
 }

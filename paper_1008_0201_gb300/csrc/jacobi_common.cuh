@@ -82,6 +82,7 @@ struct JacStepArgs {
 struct PivotParams {
   double tol;        // outer rotation threshold
   int factor;        // 0 unpivoted, 2 sign-pivoted
+  int ns_mode;       // 1: make V_P J-unitary in FP64 (Newton-Schulz); 0: leave the FP32 transform
 };
 
 // per (step, pair) record written by the pivot kernel, reduced per sweep
@@ -94,6 +95,7 @@ struct PairStat {
   int inner_sweeps;
   int ns_steps;
   int active;         // 1 iff some |a_ij| > tol sqrt(a_ii a_jj): the FP64 convergence test
+  long long cyc[4];   // SM clocks of the pivot phases: stats, Cholesky, inner sweeps, J-orth.
 };
 
 struct SweepRecord {
@@ -102,6 +104,8 @@ struct SweepRecord {
   double trace;
   long long rotations;
   long long pivots_rotated;
+  long long cyc[4];
+  long long ns_steps;
   unsigned int err;
   int pad;
 };

@@ -1,6 +1,7 @@
 // pivot.cu -- one pivot block per CTA: the square factor and the inner one-sided Jacobi.
 //
-// For the pair (p, q) of a step, with X = [G_p G_q] (m x k) and A_P = X^* X (from k_gram):
+// For the pair (p, q) of a step, with X = [G_p G_q] (m x k) and A_P = X^* X (from the gram
+// kernel):
 //  1. convergence statistics of A_P: rotate the block iff some |a_ij| > tol sqrt(a_ii a_jj);
 //  2. the Cholesky factor P^T A_P P = R^* R (Sec. 3.2), unpivoted (HF) or J_P-sign-pivoted
 //     (Algorithm 3.3, HFSC: diagonal pivoting inside the J = +1 part, then inside the Schur
@@ -9,48 +10,73 @@
 //     "one-sided manner" of Sec. 2.2), trigonometric rotations (Eq. (2.1)) for equal signs and
 //     hyperbolic ones otherwise, with the tanh = +-1 guard of Sec. 3.2, repeated until an inner
 //     sweep rotates nothing (full block algorithm);
-//  4. V_P = P W (rows permuted back, Algorithm 3.4), made J_P-unitary to FP64 accuracy.
+//  4. V_P = P W Pi (rows permuted back as Algorithm 3.4 states; Pi = the reversed order of the
+//     J = -1 columns of Algorithm 3.3), J_P-unitary to FP64 accuracy when requested.
 //
-// GB300 placement: the inner rotations run in FP32 (warp per column pair, 32 pairs at once).
-// To keep relative precision when A_P is nearly diagonal, the factor is carried as
+// GB300 placement.  The inner rotations run in FP32 (warp per column pair, up to 32 pairs at
+// once).  To keep relative precision when A_P is nearly diagonal, the factor is carried as
 //     A_P = D (I + E) D,   R = Dp + F,   W = I + Wd,
-// where D = diag(fp32(sqrt(a_ii))) is fixed, E is formed in FP64 and rounded once, and only the
-// deviations F, Wd are stored in FP32: every rotation is applied as F <- F Q + Dp (Q - I) and
-// Wd <- Wd Q + (Q - I), so the small entries keep their own relative precision.  Rotation
-// angles therefore only need FP32; the transform applied to G must be J-unitary in FP64, which
-// the Newton-Schulz correction V <- V - V J (V^* J V - J) / 2 gives (quadratic; run on the FP64
-// mma path until the residual is at rounding level).
+// where D = diag(fp32(sqrt(a_ii))) is fixed and only the deviations F, Wd are stored in FP32:
+// every rotation Q is applied as F <- F Q + Dp (Q - I) and Wd <- Wd Q + (Q - I), so small
+// entries keep their own relative precision and the angles need FP32 only.  The transform that
+// is applied to G in FP64 must be J-unitary in FP64; it is corrected by Newton-Schulz,
+//     V <- V - V J (V^T J V - J) / 2   (quadratic),
+// whose residual M = V^T J V - J is formed in FP32 from the small Wd when max|Wd| <= 2^-20 and
+// otherwise on the FP64 mma path (symmetric tiles only); the correction product itself is small
+// and is formed in FP32.
 #include "jacobi_common.cuh"
 
 namespace jac {
 
 #define PV_KM JAC_KMAX
-#define PV_LDF JAC_KMAX        // F, W column stride (floats)
-#define PV_LDS (JAC_KMAX + 1)  // Cholesky working matrix stride (floats)
-#define PV_LDV (JAC_KMAX + 1)  // FP64 V stride
-#define PV_LDM (JAC_KMAX + 1)  // FP64 M / T stride
+#define PV_LDF JAC_KMAX        // F, W column stride (floats): column c rows 2l, 2l+1 in lane l
+#define PV_LDS (JAC_KMAX + 1)  // Cholesky working matrix / FP32 scratch stride (floats)
+#define PV_LDV (JAC_KMAX + 1)  // FP64 V / M stride
 #define PV_THREADS 1024
 #define PV_WARPS 32
 
 struct PivotSmem {
-  double V[PV_KM * PV_LDV];   // A_P first (ld PV_LDV), then V_P
-  double M[PV_KM * PV_LDM];
-  double T[PV_KM * PV_LDM];
-  float S[PV_KM * PV_LDS];
+  double V[PV_KM * PV_LDV];   // A_P first, then V (physical coordinates), FP64
+  double M[PV_KM * PV_LDV];   // FP64 residual
+  float S[PV_KM * PV_LDS];    // Cholesky working matrix, later FP32 J M
   float F[PV_KM * PV_LDF];
   float W[PV_KM * PV_LDF];
-  double inva[PV_KM];
+  float Vf[PV_KM * PV_LDS];   // FP32 copy of V for the correction product
+  float cn[PV_KM];            // tracked c_i = ||r_i||^2 - s_i^2 of the inner sweep
   double invd[PV_KM];
   float dd[PV_KM];
+  float fid[PV_KM];           // fp32(1 / d_i)
   int perm[PV_KM];
   int lpos[PV_KM];
   int jphys[PV_KM];
   int jloc[PV_KM];
-  double red_d[PV_WARPS][4];
-  int red_i[PV_WARPS];
+  float red_f[PV_WARPS][4];
+  int red_i[PV_WARPS][2];
   int piv;
   int bad;
 };
+
+union F2U {
+  float2 f;
+  unsigned long long u;
+};
+
+// packed FP32 pair arithmetic (Blackwell f32x2 pipe)
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+  F2U A, B, C, D;
+  A.f = a;
+  B.f = b;
+  C.f = c;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(D.u) : "l"(A.u), "l"(B.u), "l"(C.u));
+  return D.f;
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+  F2U A, B, D;
+  A.f = a;
+  B.f = b;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(D.u) : "l"(A.u), "l"(B.u));
+  return D.f;
+}
 
 __device__ __forceinline__ void rr_inner_pair(int kk, int s, int w, int& li, int& lj) {
   // circle method on kk (even) positions: position kk-1 fixed
@@ -65,28 +91,16 @@ __device__ __forceinline__ void rr_inner_pair(int kk, int s, int w, int& li, int
   }
 }
 
-// C(i,j) = sum_r A(i,r) B(r,j) for 0 <= i, j < KP on the FP64 mma path, one 16x8 tile per warp
-// per iteration.  la/lb read shared memory, sc stores.
-template <class LA, class LB, class SC>
-__device__ __forceinline__ void cta_dmma(int KP, LA la, LB lb, SC sc) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  const int ntj = KP / 8, ntiles = (KP / 16) * ntj;
-  for (int tile = warp; tile < ntiles; tile += PV_WARPS) {
-    const int ti = tile / ntj, tj = tile % ntj;
-    double c[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int kk = 0; kk < KP; kk += 16) {
-      double av[8], bv[4];
+__device__ __forceinline__ float block_max_f(float v, PivotSmem& sm, int slot) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
-      for (int i = 0; i < 8; ++i) av[i] = la(16 * ti + g + 8 * (i & 1), kk + 4 * t + (i >> 1));
-#pragma unroll
-      for (int j = 0; j < 4; ++j) bv[j] = lb(kk + 4 * t + j, 8 * tj + g);
-      dmma16816(c, av, bv);
-    }
-    sc(16 * ti + g, 8 * tj + 2 * t, c[0]);
-    sc(16 * ti + g, 8 * tj + 2 * t + 1, c[1]);
-    sc(16 * ti + g + 8, 8 * tj + 2 * t, c[2]);
-    sc(16 * ti + g + 8, 8 * tj + 2 * t + 1, c[3]);
-  }
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if (lane == 0) sm.red_f[warp][slot] = v;
+  __syncthreads();
+  float r = 0.0f;
+  for (int w = 0; w < PV_WARPS; ++w) r = fmaxf(r, sm.red_f[w][slot]);
+  __syncthreads();
+  return r;
 }
 
 __global__ void __launch_bounds__(PV_THREADS, 1)
@@ -97,28 +111,40 @@ __global__ void __launch_bounds__(PV_THREADS, 1)
   PivotSmem& sm = *reinterpret_cast<PivotSmem*>(pv_raw);
   const int pair = blockIdx.x;
   if (pair >= *step_count) return;
+  const long long t_start = clock64();
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int p = step_pairs[2 * pair], q = step_pairs[2 * pair + 1];
   const int op = a.boff[p], wp = a.boff[p + 1] - op, oq = a.boff[q], wq = a.boff[q + 1] - oq;
   const int k = wp + wq, KP = (k + 15) & ~15;
   double* Vs = sm.V;
 
-  // ---- 1. load A_P, statistics -------------------------------------------------------------
+  // ---- 1. load A_P, scaled matrix E, statistics ----------------------------------------------
   const double* A = Ap + (size_t)pair * JAC_KMAX * JAC_KMAX;
   for (int e = tid; e < k * k; e += PV_THREADS) {
     const int i = e % k, j = e / k;
     Vs[j * PV_LDV + i] = A[j * JAC_KMAX + i];
   }
+  if (tid == 0) sm.bad = 0;
+  __syncthreads();
+  double tr = 0.0;
   if (tid < k) {
     const int col = tid < wp ? op + tid : oq + (tid - wp);
     sm.jloc[tid] = a.Js[col];
-  }
-  if (tid == 0) sm.bad = 0;
-  __syncthreads();
-  if (tid < k) {
     const double aii = Vs[tid * PV_LDV + tid];
     if (!(aii > 0.0) || !(aii < 1.0e300)) atomicOr(&sm.bad, 1);
-    sm.inva[tid] = 1.0 / aii;
+    const float d = sqrtf((float)aii);
+    const double id = 1.0 / (double)d;
+    sm.dd[tid] = d;
+    sm.invd[tid] = id;
+    sm.fid[tid] = (float)id;
+    sm.perm[tid] = tid;
+    // e_ii = a_ii / d_i^2 - 1 in FP64 (cancellation), then rounded once
+    sm.S[tid * PV_LDS + tid] = (float)(aii * id * id - 1.0);
+    tr = aii;
+  }
+  for (int e = tid; e < PV_KM * PV_LDF; e += PV_THREADS) {
+    sm.F[e] = 0.0f;
+    sm.W[e] = 0.0f;
   }
   __syncthreads();
   if (sm.bad) {
@@ -130,83 +156,80 @@ __global__ void __launch_bounds__(PV_THREADS, 1)
     }
     return;
   }
-  const double tol2 = pp.tol * pp.tol;
-  double mx = 0.0, oc = 0.0, od = 0.0, tr = 0.0;
+  // off-diagonal e_ij = a_ij / (d_i d_j) in FP32: it is the scaled off-diagonal entry
+  // |a_ij| / sqrt(a_ii a_jj) to FP32 accuracy, so it drives the statistics; only entries within
+  // 2^-12 of the threshold are re-decided in FP64.
+  const float tolf = (float)pp.tol;
+  float mx = 0.0f, oc = 0.0f, od = 0.0f;
   int cnt = 0;
   for (int e = tid; e < k * k; e += PV_THREADS) {
     const int i = e % k, j = e / k;
+    if (i == j) continue;
+    const float aij = (float)Vs[j * PV_LDV + i];
+    const float eij = aij * sm.fid[i] * sm.fid[j];
+    sm.S[j * PV_LDS + i] = eij;
     if (i < j) {
-      const double aij = Vs[j * PV_LDV + i];
-      const double a2 = aij * aij;
-      const double r2 = a2 * sm.inva[i] * sm.inva[j];
-      mx = fmax(mx, r2);
-      cnt += (r2 > tol2) ? 1 : 0;
+      const float r = fabsf(eij);
+      mx = fmaxf(mx, r);
+      bool hit = r > tolf;
+      if (fabsf(r - tolf) <= tolf * 2.44140625e-4f) {
+        const double ad = Vs[j * PV_LDV + i];
+        hit = ad * ad > pp.tol * pp.tol * Vs[i * PV_LDV + i] * Vs[j * PV_LDV + j];
+      }
+      cnt += hit ? 1 : 0;
+      const float a2 = aij * aij;
       if ((i < wp) != (j < wp)) oc += a2; else od += a2;
-    } else if (i == j) {
-      tr += Vs[j * PV_LDV + i];
     }
   }
-  mx = warp_max_d(mx);
-  oc = warp_sum_d(oc);
-  od = warp_sum_d(od);
-  tr = warp_sum_d(tr);
-  cnt = warp_sum_i(cnt);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    oc += __shfl_xor_sync(0xffffffffu, oc, o);
+    od += __shfl_xor_sync(0xffffffffu, od, o);
+    cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  }
+  if (warp < 2) tr = warp_sum_d(tr);  // k <= 64 diagonal entries live in warps 0 and 1
   if (lane == 0) {
-    sm.red_d[warp][0] = mx;
-    sm.red_d[warp][1] = oc;
-    sm.red_d[warp][2] = od;
-    sm.red_d[warp][3] = tr;
-    sm.red_i[warp] = cnt;
+    sm.red_f[warp][0] = mx;
+    sm.red_f[warp][1] = oc;
+    sm.red_f[warp][2] = od;
+    sm.red_i[warp][0] = cnt;
+    if (warp < 2) sm.M[warp] = tr;
   }
   __syncthreads();
-  mx = 0.0;
-  oc = od = tr = 0.0;
+  mx = oc = od = 0.0f;
   cnt = 0;
   for (int w = 0; w < PV_WARPS; ++w) {
-    mx = fmax(mx, sm.red_d[w][0]);
-    oc += sm.red_d[w][1];
-    od += sm.red_d[w][2];
-    tr += sm.red_d[w][3];
-    cnt += sm.red_i[w];
+    mx = fmaxf(mx, sm.red_f[w][0]);
+    oc += sm.red_f[w][1];
+    od += sm.red_f[w][2];
+    cnt += sm.red_i[w][0];
   }
   PairStat st;
-  st.max_scaled = sqrt(mx);
-  st.off2_cross = oc;
-  st.off2_diag = od;
-  st.trace = tr;
+  st.max_scaled = (double)mx;
+  st.off2_cross = (double)oc;
+  st.off2_diag = (double)od;
+  st.trace = sm.M[0] + sm.M[1];
   st.rotations = 0;
   st.inner_sweeps = 0;
   st.ns_steps = 0;
   st.active = (cnt > 0) ? 1 : 0;
+  const long long t_stats = clock64();
   if (cnt == 0) {
     if (tid == 0) {
       skip[pair] = 1;
+      st.cyc[0] = t_stats - t_start;
+      st.cyc[1] = st.cyc[2] = st.cyc[3] = 0;
       stats[pair] = st;
     }
     return;
   }
+  __syncthreads();  // red_* and the trace slots are reused below
 
   // ---- 2. scaled, optionally sign-pivoted Cholesky in FP32 -----------------------------------
-  if (tid < k) {
-    const float d = sqrtf((float)Vs[tid * PV_LDV + tid]);
-    sm.dd[tid] = d;
-    sm.invd[tid] = 1.0 / (double)d;
-    sm.perm[tid] = tid;
-    sm.jphys[tid] = sm.jloc[tid];
-  }
-  for (int e = tid; e < PV_KM * PV_LDF; e += PV_THREADS) {
-    sm.F[e] = 0.0f;
-    sm.W[e] = 0.0f;
-  }
-  __syncthreads();
-  for (int e = tid; e < k * k; e += PV_THREADS) {
-    const int i = e % k, j = e / k;
-    double v = Vs[j * PV_LDV + i] * sm.invd[i] * sm.invd[j];
-    if (i == j) v -= 1.0;
-    sm.S[j * PV_LDS + i] = (float)v;
-  }
   int npos = 0;
   for (int c = 0; c < k; ++c) npos += (sm.jloc[c] > 0) ? 1 : 0;  // J sorted: + block first
+  if (tid < k) sm.jphys[tid] = sm.jloc[tid];
   __syncthreads();
   const bool signpiv = (pp.factor == 2);
   for (int i = 0; i < k; ++i) {
@@ -240,7 +263,7 @@ __global__ void __launch_bounds__(PV_THREADS, 1)
         // symmetric swap of rows/columns i and pv of the trailing matrix, of the computed rows
         // of F (columns i and pv), and of the bookkeeping
         for (int tt = tid; tt < k; tt += PV_THREADS) {
-          if (tt >= i && tt != i && tt != pv) {
+          if (tt > i && tt != pv) {
             float x = sm.S[i * PV_LDS + tt];
             sm.S[i * PV_LDS + tt] = sm.S[pv * PV_LDS + tt];
             sm.S[pv * PV_LDS + tt] = x;
@@ -278,7 +301,7 @@ __global__ void __launch_bounds__(PV_THREADS, 1)
     // G) is treated as rank deficient.
     if (!(piv1 > 3.8146973e-6f)) {
       if (tid == 0) sm.bad = 1;
-      break;               // uniform: every thread read the same sii
+      break;  // uniform: every thread read the same sii
     }
     const float r = sqrtf(piv1);
     for (int j = i + 1 + tid; j < k; j += PV_THREADS) sm.F[j * PV_LDF + i] = sm.S[j * PV_LDS + i] / r;
@@ -306,18 +329,29 @@ __global__ void __launch_bounds__(PV_THREADS, 1)
     if (r <= c) sm.F[c * PV_LDF + r] *= sm.dd[c];
   }
   if (tid < k) {
-    int l = tid;
+    const int l = tid;
     sm.lpos[l] = (signpiv && l >= npos) ? (k - 1 - (l - npos)) : l;
   }
   __syncthreads();
+  const long long t_chol = clock64();
 
   // ---- 3. inner one-sided Jacobi (FP32, shifted representation) -----------------------------
   // inner threshold: at most half the outer one (so that a pair flagged in FP64 is rotated in
   // FP32), at least the FP32 noise level of the shifted dot products
-  const float tol_in = fmaxf(0.5f * (float)pp.tol, 64.0f * 5.9604645e-8f * (float)st.max_scaled);
+  const float tol_in = fmaxf(0.5f * tolf, 64.0f * 5.9604645e-8f * mx);
   const int kk = k + (k & 1);
+  float2* F2 = reinterpret_cast<float2*>(sm.F);
+  float2* W2 = reinterpret_cast<float2*>(sm.W);
   int total_rot = 0, inner = 0;
   for (inner = 0; inner < JAC_INNER_MAX_SWEEPS; ++inner) {
+    // c_i = 2 s_i F_ii + ||f_i||^2 recomputed at the start of every inner sweep, tracked below
+    for (int c = warp; c < k; c += PV_WARPS) {
+      const float2 f = F2[c * (PV_LDF / 2) + lane];
+      float s = f.x * f.x + f.y * f.y;
+      s = warp_sum(s);
+      if (lane == 0) sm.cn[c] = 2.0f * sm.dd[c] * sm.F[c * PV_LDF + c] + s;
+    }
+    __syncthreads();
     int my_rot = 0;
     for (int s = 0; s < kk - 1; ++s) {
       if (warp < kk / 2) {
@@ -325,28 +359,19 @@ __global__ void __launch_bounds__(PV_THREADS, 1)
         rr_inner_pair(kk, s, warp, li, lj);
         if (lj < k) {
           const int i = sm.lpos[li], j = sm.lpos[lj];
-          float* Fi = sm.F + i * PV_LDF;
-          float* Fj = sm.F + j * PV_LDF;
-          const float fi0 = Fi[lane], fi1 = Fi[lane + 32], fj0 = Fj[lane], fj1 = Fj[lane + 32];
-          float sii = fi0 * fi0 + fi1 * fi1;
-          float sjj = fj0 * fj0 + fj1 * fj1;
-          float sij = fi0 * fj0 + fi1 * fj1;
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) {
-            sii += __shfl_xor_sync(0xffffffffu, sii, o);
-            sjj += __shfl_xor_sync(0xffffffffu, sjj, o);
-            sij += __shfl_xor_sync(0xffffffffu, sij, o);
-          }
+          const float2 fi = F2[i * (PV_LDF / 2) + lane], fj = F2[j * (PV_LDF / 2) + lane];
+          float sij = fi.x * fj.x + fi.y * fj.y;
+          sij = warp_sum(sij);
           const float si = sm.dd[i], sj = sm.dd[j];
-          const float Fii = Fi[i], Fjj = Fj[j], Fji = Fi[j], Fij = Fj[i];
-          const float ci = 2.0f * si * Fii + sii, cj = 2.0f * sj * Fjj + sjj;
+          const float Fji = sm.F[i * PV_LDF + j], Fij = sm.F[j * PV_LDF + i];
+          const float ci = sm.cn[i], cj = sm.cn[j];
           const float aij = si * Fij + sj * Fji + sij;
           const float aii = si * si + ci, ajj = sj * sj + cj;
           const float beta = fabsf(aij);
           if (beta > tol_in * sqrtf(aii) * sqrtf(ajj)) {
             ++my_rot;
             const float e = (aij < 0.0f) ? -1.0f : 1.0f;
-            float q11, q12, q21, cm1;
+            float q11, q12, q21, cm1, dci, dcj;
             if (sm.jphys[i] == sm.jphys[j]) {
               // trigonometric, Eq. (2.1): cot(2 phi) = (a_jj - a_ii) / (2 |a_ij|)
               const float zeta = ((sj - si) * (sj + si) + (cj - ci)) / (2.0f * beta);
@@ -358,6 +383,8 @@ __global__ void __launch_bounds__(PV_THREADS, 1)
               q11 = c;
               q12 = e * s_;
               q21 = -e * s_;
+              dci = -t * beta;  // a_ii' = a_ii - t |a_ij|, a_jj' = a_jj + t |a_ij|
+              dcj = t * beta;
             } else {
               // hyperbolic: coth(2 phi) = -(a_ii + a_jj) / (2 |a_ij|); |tanh| < 1 guard (Sec. 3.2)
               const float zeta = -(aii + ajj) / (2.0f * beta);
@@ -376,109 +403,168 @@ __global__ void __launch_bounds__(PV_THREADS, 1)
               q11 = ch;
               q12 = e * sh;
               q21 = e * sh;
+              dci = t * beta;  // both diagonals move by t |a_ij| (the J-trace is invariant)
+              dcj = t * beta;
             }
-            const float q22 = q11;
-            float nfi0 = q11 * fi0 + q21 * fj0, nfi1 = q11 * fi1 + q21 * fj1;
-            float nfj0 = q12 * fi0 + q22 * fj0, nfj1 = q12 * fi1 + q22 * fj1;
+            const float2 Q11 = make_float2(q11, q11), Q12 = make_float2(q12, q12), Q21 = make_float2(q21, q21);
+            float2 nfi = fma2(Q11, fi, mul2(Q21, fj));
+            float2 nfj = fma2(Q11, fj, mul2(Q12, fi));
             // + Dp (Q - I): column i gets si (q11-1) at row i and sj q21 at row j; column j
             // gets si q12 at row i and sj (q22-1) at row j
-            if (lane == (i & 31)) {
-              if (i < 32) { nfi0 += si * cm1; nfj0 += si * q12; } else { nfi1 += si * cm1; nfj1 += si * q12; }
+            if (lane == (i >> 1)) {
+              if (i & 1) { nfi.y += si * cm1; nfj.y += si * q12; } else { nfi.x += si * cm1; nfj.x += si * q12; }
             }
-            if (lane == (j & 31)) {
-              if (j < 32) { nfi0 += sj * q21; nfj0 += sj * cm1; } else { nfi1 += sj * q21; nfj1 += sj * cm1; }
+            if (lane == (j >> 1)) {
+              if (j & 1) { nfi.y += sj * q21; nfj.y += sj * cm1; } else { nfi.x += sj * q21; nfj.x += sj * cm1; }
             }
-            Fi[lane] = nfi0;
-            Fi[lane + 32] = nfi1;
-            Fj[lane] = nfj0;
-            Fj[lane + 32] = nfj1;
-            float* Wi = sm.W + i * PV_LDF;
-            float* Wj = sm.W + j * PV_LDF;
-            const float wi0 = Wi[lane], wi1 = Wi[lane + 32], wj0 = Wj[lane], wj1 = Wj[lane + 32];
-            float nwi0 = q11 * wi0 + q21 * wj0, nwi1 = q11 * wi1 + q21 * wj1;
-            float nwj0 = q12 * wi0 + q22 * wj0, nwj1 = q12 * wi1 + q22 * wj1;
-            if (lane == (i & 31)) {
-              if (i < 32) { nwi0 += cm1; nwj0 += q12; } else { nwi1 += cm1; nwj1 += q12; }
+            F2[i * (PV_LDF / 2) + lane] = nfi;
+            F2[j * (PV_LDF / 2) + lane] = nfj;
+            const float2 wi = W2[i * (PV_LDF / 2) + lane], wj = W2[j * (PV_LDF / 2) + lane];
+            float2 nwi = fma2(Q11, wi, mul2(Q21, wj));
+            float2 nwj = fma2(Q11, wj, mul2(Q12, wi));
+            if (lane == (i >> 1)) {
+              if (i & 1) { nwi.y += cm1; nwj.y += q12; } else { nwi.x += cm1; nwj.x += q12; }
             }
-            if (lane == (j & 31)) {
-              if (j < 32) { nwi0 += q21; nwj0 += cm1; } else { nwi1 += q21; nwj1 += cm1; }
+            if (lane == (j >> 1)) {
+              if (j & 1) { nwi.y += q21; nwj.y += cm1; } else { nwi.x += q21; nwj.x += cm1; }
             }
-            Wi[lane] = nwi0;
-            Wi[lane + 32] = nwi1;
-            Wj[lane] = nwj0;
-            Wj[lane + 32] = nwj1;
+            W2[i * (PV_LDF / 2) + lane] = nwi;
+            W2[j * (PV_LDF / 2) + lane] = nwj;
+            if (lane == 0) {
+              sm.cn[i] = ci + dci;
+              sm.cn[j] = cj + dcj;
+            }
           }
         }
       }
       __syncthreads();
     }
-    if (lane == 0) sm.red_i[warp] = my_rot;
+    if (lane == 0) sm.red_i[warp][1] = my_rot;
     __syncthreads();
     int tot = 0;
-    for (int w = 0; w < PV_WARPS; ++w) tot += sm.red_i[w];
+    for (int w = 0; w < PV_WARPS; ++w) tot += sm.red_i[w][1];
     __syncthreads();
     total_rot += tot;
     if (tot == 0) break;
   }
   if (inner >= JAC_INNER_MAX_SWEEPS && tid == 0) atomicOr(err, JAC_DEVERR_INNER_LIMIT);
+  const long long t_inner = clock64();
 
-  // ---- 4. V_P = P (I + Wd) Pi in FP64, then J-orthogonalize ---------------------------------
+  // ---- 4. V = I + Wd (physical coordinates), J-orthogonalized in FP64 if requested ----------
+  float wm = 0.0f;
+  for (int e = tid; e < KP * KP; e += PV_THREADS) {
+    const int r = e % KP, c = e / KP;
+    const float w = (r < k && c < k) ? sm.W[c * PV_LDF + r] : 0.0f;
+    const double v = (double)w + ((r == c && r < k) ? 1.0 : 0.0);
+    Vs[c * PV_LDV + r] = v;
+    sm.Vf[c * PV_LDS + r] = (float)v;
+    wm = fmaxf(wm, fabsf(w));
+  }
+  int ns = 0;
+  if (pp.ns_mode) {
+    wm = block_max_f(wm, sm, 3);  // includes the barrier after the V build
+    const bool small_w = wm <= 9.5367431640625e-7f;  // 2^-20
+    for (int it = 0; it < 3; ++it) {
+      // residual M = V^T J V - J, J = diag(jphys) on rows and columns
+      float mloc = 0.0f;
+      if (it == 0 && small_w) {
+        // V = I + Wd: M = Wd^T J + J Wd + Wd^T J Wd.  The linear part is exact in FP32 when it
+        // cancels (Sterbenz) and rounds relative to itself otherwise; the quadratic part is at
+        // most k 2^-40 and carries FP32 relative error.  Stored as fp32(J M) directly.
+        for (int e = tid; e < KP * KP; e += PV_THREADS) {
+          const int x = e % KP, j = e / KP;
+          float mv = 0.0f;
+          if (x < k && j < k) {
+            const float jx = (float)sm.jphys[x], jj = (float)sm.jphys[j];
+            float quad = 0.0f;
+            for (int r = 0; r < k; ++r)
+              quad = fmaf(sm.W[x * PV_LDF + r] * (float)sm.jphys[r], sm.W[j * PV_LDF + r], quad);
+            mv = (sm.W[x * PV_LDF + j] * jj + jx * sm.W[j * PV_LDF + x]) + quad;
+          }
+          mloc = fmaxf(mloc, fabsf(mv));
+          sm.S[j * PV_LDS + x] = (x < k) ? (float)sm.jphys[x] * mv : 0.0f;  // (J M)[x][j]
+        }
+      } else {
+        // FP64 mma, upper tiles (8 tj + 7 >= 16 ti) and the mirror of the strict lower part
+        const int g = lane >> 2, t = lane & 3;
+        const int ntj = KP / 8, ntiles = (KP / 16) * ntj;
+        for (int tile = warp; tile < ntiles; tile += PV_WARPS) {
+          const int ti = tile / ntj, tj = tile % ntj;
+          if (8 * tj + 7 < 16 * ti) continue;
+          double c4[4] = {0.0, 0.0, 0.0, 0.0};
+          for (int kq = 0; kq < KP; kq += 16) {
+            double av[8], bv[4];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) av[u] = Vs[(16 * ti + g + 8 * (u & 1)) * PV_LDV + kq + 4 * t + (u >> 1)];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int r = kq + 4 * t + u;
+              const double v = Vs[(8 * tj + g) * PV_LDV + r];
+              bv[u] = (r < k && sm.jphys[r] < 0) ? -v : v;
+            }
+            dmma16816(c4, av, bv);
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int i = 16 * ti + g + 8 * (u >> 1), j = 8 * tj + 2 * t + (u & 1);
+            double v = c4[u];
+            if (i == j && i < k) v -= (sm.jphys[i] < 0) ? -1.0 : 1.0;
+            sm.M[j * PV_LDV + i] = v;
+            sm.M[i * PV_LDV + j] = v;
+          }
+        }
+        __syncthreads();
+        for (int e = tid; e < KP * KP; e += PV_THREADS) {
+          const int x = e % KP, j = e / KP;
+          const double mv = sm.M[j * PV_LDV + x];
+          mloc = fmaxf(mloc, (float)fabs(mv));
+          sm.S[j * PV_LDS + x] = (x < k) ? (float)((sm.jphys[x] < 0) ? -mv : mv) : 0.0f;
+        }
+      }
+      const float mm = block_max_f(mloc, sm, 0);
+      if (mm <= 4.0e-16f) break;
+      // V <- V - V (J M) / 2: the correction is O(|M|), formed in FP32 from the FP32 copy of V
+      for (int e = tid; e < KP * KP; e += PV_THREADS) {
+        const int r = e % KP, j = e / KP;
+        float s = 0.0f;
+        for (int x = 0; x < k; ++x) s = fmaf(sm.Vf[x * PV_LDS + r], sm.S[j * PV_LDS + x], s);
+        Vs[j * PV_LDV + r] -= 0.5 * (double)s;
+      }
+      ++ns;
+      __syncthreads();
+      // predicted residual after this step: quadratic term + FP32 rounding of the correction
+      if (mm * mm + 1.0e-6f * mm <= 2.0e-16f) break;
+      for (int e = tid; e < KP * KP; e += PV_THREADS) {
+        const int r = e % KP, c = e / KP;
+        sm.Vf[c * PV_LDS + r] = (float)Vs[c * PV_LDV + r];
+      }
+      __syncthreads();
+    }
+  } else {
+    __syncthreads();
+  }
+  const long long t_ns = clock64();
+  // V_P = P V Pi: V_P[perm[r]][l] = V[r][lpos[l]]
+  double* out = vp + (size_t)pair * JAC_KMAX * JAC_KMAX;
   for (int e = tid; e < KP * KP; e += PV_THREADS) {
     const int r = e % KP, l = e / KP;
     double v = 0.0;
     int row = r;
     if (r < k && l < k) {
-      const int c = sm.lpos[l];
-      v = (double)sm.W[c * PV_LDF + r] + ((r == c) ? 1.0 : 0.0);
+      v = Vs[sm.lpos[l] * PV_LDV + r];
       row = sm.perm[r];
     }
-    Vs[l * PV_LDV + row] = v;
-  }
-  __syncthreads();
-  int ns = 0;
-  const double ns_thresh = 8.881784197001252e-16;  // 2^-50
-  for (int it = 0; it < 4; ++it) {
-    // M = V^T J V - J   (J = J_P on rows and on columns: the permutations keep the signs)
-    cta_dmma(
-        KP, [&](int i, int r) { return Vs[i * PV_LDV + r]; },
-        [&](int r, int j) { return (r < k && sm.jloc[r] < 0) ? -Vs[j * PV_LDV + r] : Vs[j * PV_LDV + r]; },
-        [&](int i, int j, double v) {
-          if (i == j && i < k) v -= (sm.jloc[i] < 0) ? -1.0 : 1.0;
-          sm.M[j * PV_LDM + i] = v;
-        });
-    __syncthreads();
-    double mloc = 0.0;
-    for (int e = tid; e < KP * KP; e += PV_THREADS) mloc = fmax(mloc, fabs(sm.M[(e / KP) * PV_LDM + e % KP]));
-    mloc = warp_max_d(mloc);
-    if (lane == 0) sm.red_d[warp][0] = mloc;
-    __syncthreads();
-    double mm = 0.0;
-    for (int w = 0; w < PV_WARPS; ++w) mm = fmax(mm, sm.red_d[w][0]);
-    __syncthreads();
-    if (mm < ns_thresh) break;
-    // T = V (J M)
-    cta_dmma(
-        KP, [&](int r, int x) { return Vs[x * PV_LDV + r]; },
-        [&](int x, int j) { return (x < k && sm.jloc[x] < 0) ? -sm.M[j * PV_LDM + x] : sm.M[j * PV_LDM + x]; },
-        [&](int r, int j, double v) { sm.T[j * PV_LDM + r] = v; });
-    __syncthreads();
-    for (int e = tid; e < KP * KP; e += PV_THREADS) {
-      const int r = e % KP, j = e / KP;
-      Vs[j * PV_LDV + r] -= 0.5 * sm.T[j * PV_LDM + r];
-    }
-    __syncthreads();
-    ++ns;
-  }
-  double* out = vp + (size_t)pair * JAC_KMAX * JAC_KMAX;
-  for (int e = tid; e < KP * KP; e += PV_THREADS) {
-    const int r = e % KP, j = e / KP;
-    out[j * JAC_KMAX + r] = Vs[j * PV_LDV + r];
+    out[l * JAC_KMAX + row] = v;
   }
   if (tid == 0) {
     skip[pair] = 0;
     st.rotations = total_rot;
     st.inner_sweeps = inner + 1;
     st.ns_steps = ns;
+    st.cyc[0] = t_stats - t_start;
+    st.cyc[1] = t_chol - t_stats;
+    st.cyc[2] = t_inner - t_chol;
+    st.cyc[3] = t_ns - t_inner;
     stats[pair] = st;
   }
 }

@@ -17,9 +17,9 @@ namespace jac {
 __global__ void k_sweep_reduce(const PairStat* __restrict__ stats, const int* __restrict__ counts, int nsteps,
                                int half, int nb, const unsigned* __restrict__ err, SweepRecord* __restrict__ rec) {
   __shared__ double sm_d[8][3];
-  __shared__ long long sm_l[8][2];
+  __shared__ long long sm_l[8][7];
   double mx = 0.0, off2 = 0.0, tr = 0.0;
-  long long rot = 0, piv = 0;
+  long long rot = 0, piv = 0, cy[4] = {0, 0, 0, 0}, ns = 0;
   const double wdiag = 1.0 / (double)(nb > 1 ? nb - 1 : 1);
   for (int e = threadIdx.x; e < nsteps * half; e += blockDim.x) {
     const int s = e / half, slot = e % half;
@@ -30,6 +30,8 @@ __global__ void k_sweep_reduce(const PairStat* __restrict__ stats, const int* __
     tr += wdiag * st.trace;
     rot += st.rotations;
     piv += st.active;
+    ns += st.ns_steps;
+    for (int u = 0; u < 4; ++u) cy[u] += st.cyc[u];
   }
   mx = warp_max_d(mx);
   off2 = warp_sum_d(off2);
@@ -38,6 +40,8 @@ __global__ void k_sweep_reduce(const PairStat* __restrict__ stats, const int* __
   for (int o = 16; o > 0; o >>= 1) {
     rot += __shfl_xor_sync(0xffffffffu, rot, o);
     piv += __shfl_xor_sync(0xffffffffu, piv, o);
+    ns += __shfl_xor_sync(0xffffffffu, ns, o);
+    for (int u = 0; u < 4; ++u) cy[u] += __shfl_xor_sync(0xffffffffu, cy[u], o);
   }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (lane == 0) {
@@ -46,6 +50,8 @@ __global__ void k_sweep_reduce(const PairStat* __restrict__ stats, const int* __
     sm_d[warp][2] = tr;
     sm_l[warp][0] = rot;
     sm_l[warp][1] = piv;
+    sm_l[warp][2] = ns;
+    for (int u = 0; u < 4; ++u) sm_l[warp][3 + u] = cy[u];
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -56,6 +62,8 @@ __global__ void k_sweep_reduce(const PairStat* __restrict__ stats, const int* __
       r.trace += sm_d[w][2];
       r.rotations += sm_l[w][0];
       r.pivots_rotated += sm_l[w][1];
+      r.ns_steps += sm_l[w][2];
+      for (int u = 0; u < 4; ++u) r.cyc[u] += sm_l[w][3 + u];
     }
     r.err = *err;
     *rec = r;
@@ -110,13 +118,22 @@ __global__ void k_colnorm(const double* __restrict__ Gw, int mp, int n, const in
 
 // rank[c] = #{l : lam[l] < lam[c] or (lam[l] == lam[c] and l < c)}: ascending order, ties by
 // internal index (the stable J sort keeps input order within a sign).
+// Keys are the order-preserving unsigned images of the doubles (flip all bits of negatives,
+// the sign bit of the rest), so the n^2 comparisons are integer work.
+__device__ __forceinline__ unsigned long long order_key(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
 __global__ void k_rank(const double* __restrict__ lam, int n, int* __restrict__ rank) {
+  extern __shared__ unsigned long long keys[];
+  for (int l = threadIdx.x; l < n; l += blockDim.x) keys[l] = order_key(lam[l]);
+  __syncthreads();
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n) return;
-  const double v = lam[c];
+  const unsigned long long v = keys[c];
   int r = 0;
   for (int l = 0; l < n; ++l) {
-    const double u = lam[l];
+    const unsigned long long u = keys[l];
     r += (u < v || (u == v && l < c)) ? 1 : 0;
   }
   rank[c] = r;

@@ -103,7 +103,6 @@ __global__ void k_sched_cycle_weight(int nb, const double* __restrict__ w, int* 
   const int half = nb / 2;
   int* order = order_g;  // global scratch [npairs]: rank -> pair id
   int* busy = sh_sched;  // [nb]
-  __shared__ int s_done_count;
   // pair id x <-> (p, q) in enumeration order
   // 1. rank each pair: number of pairs that come before it in the sorted order
   for (int x = threadIdx.x; x < npairs; x += blockDim.x) {
@@ -192,84 +191,66 @@ __global__ void k_sched_cycle_weight(int nb, const double* __restrict__ w, int* 
       ++step;
       __syncwarp();
     }
-    if (lane == 0) {
-      s_done_count = left;
-      *nsteps_out = (left == 0) ? step : -1;
-    }
+    if (lane == 0) *nsteps_out = (left == 0) ? step : -1;
   }
-  __syncthreads();
-  // restore order[] (not needed by callers, keeps the scratch reusable)
-  (void)s_done_count;
 }
 
-// Block weights for the per-cycle ordering: w[p*nb+q] = ||G_p^* G_q||_F^2 / (||G_p||_F^2 ||G_q||_F^2)
-// One CTA (4 warps) per pair p < q (grid = npairs); FP64 mma over all rows.  Block widths <= 32.
-__global__ void k_block_weights(const double* __restrict__ Gw, int mp, int nb, const int* __restrict__ boff,
-                                double* __restrict__ w) {
-  __shared__ double sX[2][16][33];  // [block][row][col] chunk of 16 rows
-  __shared__ double red[4][3];
+// Block weights for the per-cycle ordering, w[p*nb+q] = ||G_p^* G_q||_F^2 / (||G_p||_F^2 ||G_q||_F^2),
+// from an FP32 copy of G (the weights only rank the pairs).  One CTA (256 threads) per pair
+// p < q; thread (ty = tid / 16, tx = tid % 16) owns a 2 x 2 block of the <= 32 x 32 product.
+__global__ void k_block_weights32(const float* __restrict__ G32, int mp, int nb, const int* __restrict__ boff,
+                                  double* __restrict__ w) {
+  __shared__ float xp[32][33], xq[32][33];
+  __shared__ float red[8][3];
   const int npairs = nb * (nb - 1) / 2;
-  int x = blockIdx.x;
+  const int x = blockIdx.x;
   if (x >= npairs) return;
   int p = 0, rem = x;
   while (rem >= nb - 1 - p) {
     rem -= nb - 1 - p;
     ++p;
   }
-  int q = p + 1 + rem;
+  const int q = p + 1 + rem;
   const int op = boff[p], wp = boff[p + 1] - op, oq = boff[q], wq = boff[q + 1] - oq;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  // warp w computes the 16x8 tile (rows 16*(w>>2)... of the 32x32 product G_p^T G_q:
-  // 32x32 = 2 row tiles x 4 col tiles = 8 tiles, 2 per warp
-  double acc[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
-  double np2 = 0.0, nq2 = 0.0;
-  for (int r0 = 0; r0 < mp; r0 += 16) {
-    for (int i = threadIdx.x; i < 16 * 32; i += blockDim.x) {
-      int r = i & 15, c = i >> 4;
-      sX[0][r][c] = (c < wp) ? Gw[(size_t)(op + c) * mp + r0 + r] : 0.0;
-      sX[1][r][c] = (c < wq) ? Gw[(size_t)(oq + c) * mp + r0 + r] : 0.0;
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  float acc[2][2] = {{0.f, 0.f}, {0.f, 0.f}}, np2 = 0.f, nq2 = 0.f;
+  for (int r0 = 0; r0 < mp; r0 += 32) {
+    __syncthreads();
+    for (int idx = tid; idx < 32 * 32; idx += 256) {
+      const int r = idx & 31, c = idx >> 5;
+      xp[r][c] = (c < wp && r0 + r < mp) ? G32[(size_t)(op + c) * mp + r0 + r] : 0.f;
+      xq[r][c] = (c < wq && r0 + r < mp) ? G32[(size_t)(oq + c) * mp + r0 + r] : 0.f;
     }
     __syncthreads();
-    // column norms (threads 0..31 for p, 32..63 for q)
-    if (threadIdx.x < 64) {
-      int b = threadIdx.x >> 5, c = threadIdx.x & 31;
-      double s = 0.0;
-#pragma unroll
-      for (int r = 0; r < 16; ++r) s += sX[b][r][c] * sX[b][r][c];
-      if (b == 0) np2 += s; else nq2 += s;
+    for (int r = 0; r < 32; ++r) {
+      const float a0 = xp[r][2 * ty], a1 = xp[r][2 * ty + 1], b0 = xq[r][2 * tx], b1 = xq[r][2 * tx + 1];
+      acc[0][0] = fmaf(a0, b0, acc[0][0]);
+      acc[0][1] = fmaf(a0, b1, acc[0][1]);
+      acc[1][0] = fmaf(a1, b0, acc[1][0]);
+      acc[1][1] = fmaf(a1, b1, acc[1][1]);
     }
-#pragma unroll
-    for (int tt = 0; tt < 2; ++tt) {
-      int tile = warp * 2 + tt;       // 0..7
-      int ti = tile >> 2, tj = tile & 3;
-      double a[8], bb[4];
-#pragma unroll
-      for (int i = 0; i < 8; ++i) a[i] = sX[0][4 * t + (i >> 1)][16 * ti + g + 8 * (i & 1)];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) bb[j] = sX[1][4 * t + j][8 * tj + g];
-      dmma16816(acc[tt], a, bb);
+    if (tid < 32) {
+      for (int r = 0; r < 32; ++r) np2 = fmaf(xp[r][tid], xp[r][tid], np2);
+    } else if (tid < 64) {
+      for (int r = 0; r < 32; ++r) nq2 = fmaf(xq[r][tid - 32], xq[r][tid - 32], nq2);
     }
-    __syncthreads();
   }
-  double fro = 0.0;
-#pragma unroll
-  for (int tt = 0; tt < 2; ++tt)
-#pragma unroll
-    for (int i = 0; i < 4; ++i) fro += acc[tt][i] * acc[tt][i];
-  fro = warp_sum_d(fro);
-  if (threadIdx.x < 64) {
-    // reduce the column norms of this lane's block
-    double v = (threadIdx.x < 32) ? np2 : nq2;
-    v = warp_sum_d(v);
-    if (lane == 0) red[warp][1] = v;
+  float f = acc[0][0] * acc[0][0] + acc[0][1] * acc[0][1] + acc[1][0] * acc[1][0] + acc[1][1] * acc[1][1];
+  f = warp_sum(f);
+  np2 = warp_sum(np2);
+  nq2 = warp_sum(nq2);
+  const int warp = tid >> 5, lane = tid & 31;
+  if (lane == 0) {
+    red[warp][0] = f;
+    red[warp][1] = np2;
+    red[warp][2] = nq2;
   }
-  if (lane == 0) red[warp][0] = fro;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double f = red[0][0] + red[1][0] + red[2][0] + red[3][0];
-    double a = red[0][1], b = red[1][1];
-    double den = a * b;
-    w[p * nb + q] = (den > 0.0) ? f / den : 0.0;
+  if (tid == 0) {
+    float ff = 0.f;
+    for (int u = 0; u < 8; ++u) ff += red[u][0];
+    const double den = (double)red[0][1] * (double)red[1][2];
+    w[p * nb + q] = (den > 0.0) ? (double)ff / den : 0.0;
   }
 }
 

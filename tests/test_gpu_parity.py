@@ -48,6 +48,43 @@ def test_config2_hyperbolic_512(cuda_dev, ordering, factor):
     print("C2", ordering, factor, out["info"], r)
 
 
+@pytest.mark.parametrize("ordering", ["round_robin", "cycle_weight", "modulus"])
+@pytest.mark.parametrize("factor", ["chol", "chol_signpiv"])
+def test_config2_mixed_precision(cuda_dev, ordering, factor):
+    """FP32 sweeps, FP64 J-orthogonalization of V, FP64 polish: same tolerances as FP64."""
+    from paper_1008_0201_gb300 import inputs
+
+    G, J = inputs.config2_hyperbolic()
+    out = run(G, J, cuda_dev, block_w=32, ordering=ordering, factor=factor, precision="fp32")
+    assert out["status"] == 0, out["info"]
+    assert out["info"]["lowp_sweeps"] >= 1
+    r = compare(G, J, out)
+    print("C2-mixed", ordering, factor, out["info"], r)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_config1_precisions(cuda_dev, precision):
+    from paper_1008_0201_gb300 import inputs
+
+    G, J = inputs.config1_pd()
+    out = run(G, None, cuda_dev, block_w=8, precision=precision)
+    assert out["status"] == 0, out["info"]
+    compare(G, J, out)
+
+
+@pytest.mark.parametrize("m,n,w,frac,prec", [(130, 100, 16, 0.4, "fp32"), (37, 37, 5, 0.5, "fp32"),
+                                             (200, 61, 7, 0.0, "fp32")])
+def test_ragged_mixed(cuda_dev, m, n, w, frac, prec):
+    g = np.random.default_rng(2000 + m * 7 + n)
+    G = g.standard_normal((m, n))
+    J = np.ones(n, dtype=np.int8)
+    k = int(round(frac * n))
+    J[g.choice(n, size=k, replace=False)] = -1
+    out = run(G, J, cuda_dev, block_w=w, ordering="cycle_weight", precision=prec)
+    assert out["status"] == 0, out["info"]
+    compare(G, J, out)
+
+
 @pytest.mark.parametrize("m,n,w,frac", [(130, 100, 16, 0.4), (37, 37, 5, 0.5), (200, 61, 7, 0.0),
                                         (48, 33, 32, 0.3), (17, 3, 1, 0.34), (64, 2, 1, 0.5)])
 def test_ragged_shapes(cuda_dev, m, n, w, frac):
