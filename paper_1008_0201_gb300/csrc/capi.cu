@@ -439,6 +439,7 @@ int solve(int m, int n, int dtype, void* Gv, int ldg, const int8_t* Jdev, const 
     ck(cudaMemcpyAsync(&hrec, L.rec, sizeof(SweepRecord), cudaMemcpyDeviceToHost, st));
     ck(cudaStreamSynchronize(st));
     if (status != JAC_OK) break;
+    if (info && sweeps < 64) info->sweep_max_scaled[sweeps] = hrec.max_scaled;
     ++sweeps;
     last_steps = nsteps;
     rot_total += hrec.rotations;
@@ -515,6 +516,7 @@ int solve(int m, int n, int dtype, void* Gv, int ldg, const int8_t* Jdev, const 
   if (cudaStreamSynchronize(st) != cudaSuccess && status == JAC_OK) status = JAC_ECUDA;
   prof.finish();
   if (info) {
+    for (int u = sweeps; u < 64; ++u) info->sweep_max_scaled[u] = 0.0;
     info->sweeps = sweeps;
     info->converged = converged;
     info->status = status;

@@ -232,34 +232,34 @@ __global__ void __launch_bounds__(PV_THREADS, 1)
   if (tid < k) sm.jphys[tid] = sm.jloc[tid];
   __syncthreads();
   const bool signpiv = (pp.factor == 2);
+  const int cx = tid & 63, cy = tid >> 6;  // 2-D map of the trailing update: column cx, rows cy + 16 u
   for (int i = 0; i < k; ++i) {
     if (signpiv) {
-      if (warp == 0) {
-        const int hi = (i < npos) ? npos : k;
-        float best = -1.0f;
-        int bj = i;
-        for (int j = i + lane; j < hi; j += 32) {
-          const float dj = sm.dd[j];
-          const float v = dj * dj * (1.0f + sm.S[j * PV_LDS + j]);
-          if (v > best) {
-            best = v;
-            bj = j;
-          }
+      // every warp finds the pivot itself (largest unscaled Schur diagonal d_j^2 (1 + s_jj) in the
+      // sign group of step i): a barrier is needed only when a swap follows
+      const int hi = (i < npos) ? npos : k;
+      float best = -1.0f;
+      int bj = i;
+      for (int j = i + lane; j < hi; j += 32) {
+        const float dj = sm.dd[j];
+        const float v = dj * dj * (1.0f + sm.S[j * PV_LDS + j]);
+        if (v > best) {
+          best = v;
+          bj = j;
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-          const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
-          if (ob > best || (ob == best && oj < bj)) {
-            best = ob;
-            bj = oj;
-          }
-        }
-        if (lane == 0) sm.piv = bj;
       }
-      __syncthreads();
-      const int pv = sm.piv;
-      if (pv != i) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
+        if (ob > best || (ob == best && oj < bj)) {
+          best = ob;
+          bj = oj;
+        }
+      }
+      const int pv = bj;
+      if (pv != i) {  // uniform: every warp computed the same pv from the same values
+        __syncthreads();  // all warps have read the diagonal before it is permuted
         // symmetric swap of rows/columns i and pv of the trailing matrix, of the computed rows
         // of F (columns i and pv), and of the bookkeeping
         for (int tt = tid; tt < k; tt += PV_THREADS) {
@@ -303,14 +303,14 @@ __global__ void __launch_bounds__(PV_THREADS, 1)
       if (tid == 0) sm.bad = 1;
       break;  // uniform: every thread read the same sii
     }
-    const float r = sqrtf(piv1);
-    for (int j = i + 1 + tid; j < k; j += PV_THREADS) sm.F[j * PV_LDF + i] = sm.S[j * PV_LDS + i] / r;
+    const float r = sqrtf(piv1), ipiv = 1.0f / piv1;
+    // row i of F~ and the trailing update read only row i of S, which this step does not write
+    if (cy == 0 && cx > i && cx < k) sm.F[cx * PV_LDF + i] = sm.S[cx * PV_LDS + i] / r;
     if (tid == 0) sm.F[i * PV_LDF + i] = sii / (1.0f + r);
-    __syncthreads();
-    const int nt = k - i - 1;
-    for (int e = tid; e < nt * nt; e += PV_THREADS) {
-      const int jj = i + 1 + e % nt, ll = i + 1 + e / nt;
-      sm.S[ll * PV_LDS + jj] -= sm.F[jj * PV_LDF + i] * sm.F[ll * PV_LDF + i];
+    if (cx > i && cx < k) {
+      const float sij = sm.S[cx * PV_LDS + i] * ipiv;
+      for (int ll = i + 1 + cy; ll < k; ll += PV_THREADS / 64)
+        sm.S[ll * PV_LDS + cx] -= sij * sm.S[ll * PV_LDS + i];
     }
     __syncthreads();
   }
@@ -353,99 +353,132 @@ __global__ void __launch_bounds__(PV_THREADS, 1)
     }
     __syncthreads();
     int my_rot = 0;
+    float my_max = 0.0f;  // largest scaled |a_ij| rotated by this warp in this sweep
+    // the pair of step 0; the pair of step s + 1 is fetched while step s runs
+    int i = 0, j = 0;
+    bool act = false;
+    if (warp < kk / 2) {
+      int li, lj;
+      rr_inner_pair(kk, 0, warp, li, lj);
+      act = lj < k;
+      if (act) {
+        i = sm.lpos[li];
+        j = sm.lpos[lj];
+      }
+    }
     for (int s = 0; s < kk - 1; ++s) {
-      if (warp < kk / 2) {
-        int li, lj;
-        rr_inner_pair(kk, s, warp, li, lj);
-        if (lj < k) {
-          const int i = sm.lpos[li], j = sm.lpos[lj];
-          const float2 fi = F2[i * (PV_LDF / 2) + lane], fj = F2[j * (PV_LDF / 2) + lane];
-          float sij = fi.x * fj.x + fi.y * fj.y;
-          sij = warp_sum(sij);
-          const float si = sm.dd[i], sj = sm.dd[j];
-          const float Fji = sm.F[i * PV_LDF + j], Fij = sm.F[j * PV_LDF + i];
-          const float ci = sm.cn[i], cj = sm.cn[j];
-          const float aij = si * Fij + sj * Fji + sij;
-          const float aii = si * si + ci, ajj = sj * sj + cj;
-          const float beta = fabsf(aij);
-          if (beta > tol_in * sqrtf(aii) * sqrtf(ajj)) {
-            ++my_rot;
-            const float e = (aij < 0.0f) ? -1.0f : 1.0f;
-            float q11, q12, q21, cm1, dci, dcj;
-            if (sm.jphys[i] == sm.jphys[j]) {
-              // trigonometric, Eq. (2.1): cot(2 phi) = (a_jj - a_ii) / (2 |a_ij|)
-              const float zeta = ((sj - si) * (sj + si) + (cj - ci)) / (2.0f * beta);
-              const float az = fabsf(zeta);
-              const float t = (az > 1.0e18f) ? 0.5f / zeta : copysignf(1.0f, zeta) / (az + sqrtf(1.0f + zeta * zeta));
-              const float c = 1.0f / sqrtf(1.0f + t * t);
-              const float s_ = t * c;
-              cm1 = -(s_ * s_) / (1.0f + c);  // c - 1
-              q11 = c;
-              q12 = e * s_;
-              q21 = -e * s_;
-              dci = -t * beta;  // a_ii' = a_ii - t |a_ij|, a_jj' = a_jj + t |a_ij|
-              dcj = t * beta;
-            } else {
-              // hyperbolic: coth(2 phi) = -(a_ii + a_jj) / (2 |a_ij|); |tanh| < 1 guard (Sec. 3.2)
-              const float zeta = -(aii + ajj) / (2.0f * beta);
-              const float az = fabsf(zeta);
-              float t;
-              if (az > 1.0e18f) {
-                t = 0.5f / zeta;
-              } else {
-                const float r2 = (az - 1.0f) * (az + 1.0f);
-                t = (r2 > 0.0f) ? copysignf(1.0f, zeta) / (az + sqrtf(r2)) : copysignf(1.0f, zeta);
-              }
-              if (!(fabsf(t) < 1.0f) || !((1.0f - t) * (1.0f + t) > 0.0f)) t = copysignf(0.9f, t);
-              const float ch = 1.0f / sqrtf((1.0f - t) * (1.0f + t));
-              const float sh = t * ch;
-              cm1 = (sh * sh) / (1.0f + ch);  // ch - 1
-              q11 = ch;
-              q12 = e * sh;
-              q21 = e * sh;
-              dci = t * beta;  // both diagonals move by t |a_ij| (the J-trace is invariant)
-              dcj = t * beta;
-            }
-            const float2 Q11 = make_float2(q11, q11), Q12 = make_float2(q12, q12), Q21 = make_float2(q21, q21);
-            float2 nfi = fma2(Q11, fi, mul2(Q21, fj));
-            float2 nfj = fma2(Q11, fj, mul2(Q12, fi));
-            // + Dp (Q - I): column i gets si (q11-1) at row i and sj q21 at row j; column j
-            // gets si q12 at row i and sj (q22-1) at row j
-            if (lane == (i >> 1)) {
-              if (i & 1) { nfi.y += si * cm1; nfj.y += si * q12; } else { nfi.x += si * cm1; nfj.x += si * q12; }
-            }
-            if (lane == (j >> 1)) {
-              if (j & 1) { nfi.y += sj * q21; nfj.y += sj * cm1; } else { nfi.x += sj * q21; nfj.x += sj * cm1; }
-            }
-            F2[i * (PV_LDF / 2) + lane] = nfi;
-            F2[j * (PV_LDF / 2) + lane] = nfj;
-            const float2 wi = W2[i * (PV_LDF / 2) + lane], wj = W2[j * (PV_LDF / 2) + lane];
-            float2 nwi = fma2(Q11, wi, mul2(Q21, wj));
-            float2 nwj = fma2(Q11, wj, mul2(Q12, wi));
-            if (lane == (i >> 1)) {
-              if (i & 1) { nwi.y += cm1; nwj.y += q12; } else { nwi.x += cm1; nwj.x += q12; }
-            }
-            if (lane == (j >> 1)) {
-              if (j & 1) { nwi.y += q21; nwj.y += cm1; } else { nwi.x += q21; nwj.x += cm1; }
-            }
-            W2[i * (PV_LDF / 2) + lane] = nwi;
-            W2[j * (PV_LDF / 2) + lane] = nwj;
-            if (lane == 0) {
-              sm.cn[i] = ci + dci;
-              sm.cn[j] = cj + dcj;
-            }
+      if (act) {
+        const float2 fi = F2[i * (PV_LDF / 2) + lane], fj = F2[j * (PV_LDF / 2) + lane];
+        const float si = sm.dd[i], sj = sm.dd[j];
+        const float Fji = sm.F[i * PV_LDF + j], Fij = sm.F[j * PV_LDF + i];
+        const float ci = sm.cn[i], cj = sm.cn[j];
+        const bool same = sm.jphys[i] == sm.jphys[j];
+        float sij = fi.x * fj.x + fi.y * fj.y;
+        sij = warp_sum(sij);
+        const float aij = si * Fij + sj * Fji + sij;
+        const float aii = fmaf(si, si, ci), ajj = fmaf(sj, sj, cj);
+        const float beta = fabsf(aij);
+        const float scaled = beta * rsqrtf(aii) * rsqrtf(ajj);
+        if (scaled > tol_in) {
+          ++my_rot;
+          my_max = fmaxf(my_max, scaled);
+          const float e = (aij < 0.0f) ? -1.0f : 1.0f;
+          float q11, q12, q21, cm1, dci, dcj;
+          if (same) {
+            // trigonometric, Eq. (2.1): cot(2 phi) = (a_jj - a_ii) / (2 |a_ij|), i.e.
+            // t = sign(a_jj - a_ii) 2|a_ij| / (|a_jj - a_ii| + sqrt((a_jj - a_ii)^2 + 4 |a_ij|^2)),
+            // evaluated after an exact power-of-two scaling of both terms into [1, 4)
+            const float num = (sj - si) * (sj + si) + (cj - ci);
+            const float mxv = fmaxf(fabsf(num), 2.0f * beta);
+            const float sc = __int_as_float(0x7f000000 - (__float_as_int(mxv) & 0x7f800000));
+            const float nu = num * sc, b2 = 2.0f * beta * sc;
+            const float den = fabsf(nu) + sqrtf(fmaf(nu, nu, b2 * b2));
+            const float t = copysignf(__fdividef(b2, den), num);
+            const float c = rsqrtf(fmaf(t, t, 1.0f));
+            const float s_ = t * c;
+            cm1 = -__fdividef(s_ * s_, 1.0f + c);  // c - 1
+            q11 = c;
+            q12 = e * s_;
+            q21 = -e * s_;
+            dci = -t * beta;  // a_ii' = a_ii - t |a_ij|, a_jj' = a_jj + t |a_ij|
+            dcj = t * beta;
+          } else {
+            // hyperbolic: coth(2 phi) = -(a_ii + a_jj) / (2 |a_ij|), i.e.
+            // t = -2|a_ij| / (a_ii + a_jj + sqrt((a_ii + a_jj - 2|a_ij|)(a_ii + a_jj + 2|a_ij|))),
+            // with the |tanh| < 1 guard of Sec. 3.2
+            const float apd = aii + ajj;
+            const float sc = __int_as_float(0x7f000000 - (__float_as_int(apd) & 0x7f800000));
+            const float ap = apd * sc, b2 = 2.0f * beta * sc;
+            const float r2 = (ap - b2) * (ap + b2);
+            float t = (r2 > 0.0f) ? -__fdividef(b2, ap + sqrtf(r2)) : -1.0f;
+            if (!(fabsf(t) < 1.0f) || !((1.0f - t) * (1.0f + t) > 0.0f)) t = copysignf(0.9f, t);
+            const float ch = rsqrtf((1.0f - t) * (1.0f + t));
+            const float sh = t * ch;
+            cm1 = __fdividef(sh * sh, 1.0f + ch);  // ch - 1
+            q11 = ch;
+            q12 = e * sh;
+            q21 = e * sh;
+            dci = t * beta;  // both diagonals move by t |a_ij| (the J-trace is invariant)
+            dcj = t * beta;
           }
+          const float2 Q11 = make_float2(q11, q11), Q12 = make_float2(q12, q12), Q21 = make_float2(q21, q21);
+          float2 nfi = fma2(Q11, fi, mul2(Q21, fj));
+          float2 nfj = fma2(Q11, fj, mul2(Q12, fi));
+          // + Dp (Q - I): column i gets si (q11-1) at row i and sj q21 at row j; column j
+          // gets si q12 at row i and sj (q22-1) at row j
+          if (lane == (i >> 1)) {
+            if (i & 1) { nfi.y += si * cm1; nfj.y += si * q12; } else { nfi.x += si * cm1; nfj.x += si * q12; }
+          }
+          if (lane == (j >> 1)) {
+            if (j & 1) { nfi.y += sj * q21; nfj.y += sj * cm1; } else { nfi.x += sj * q21; nfj.x += sj * cm1; }
+          }
+          F2[i * (PV_LDF / 2) + lane] = nfi;
+          F2[j * (PV_LDF / 2) + lane] = nfj;
+          const float2 wi = W2[i * (PV_LDF / 2) + lane], wj = W2[j * (PV_LDF / 2) + lane];
+          float2 nwi = fma2(Q11, wi, mul2(Q21, wj));
+          float2 nwj = fma2(Q11, wj, mul2(Q12, wi));
+          if (lane == (i >> 1)) {
+            if (i & 1) { nwi.y += cm1; nwj.y += q12; } else { nwi.x += cm1; nwj.x += q12; }
+          }
+          if (lane == (j >> 1)) {
+            if (j & 1) { nwi.y += q21; nwj.y += cm1; } else { nwi.x += q21; nwj.x += cm1; }
+          }
+          W2[i * (PV_LDF / 2) + lane] = nwi;
+          W2[j * (PV_LDF / 2) + lane] = nwj;
+          if (lane == 0) {
+            sm.cn[i] = ci + dci;
+            sm.cn[j] = cj + dcj;
+          }
+        }
+      }
+      // next step's pair (lpos is constant during the inner sweeps)
+      if (warp < kk / 2 && s + 1 < kk - 1) {
+        int li, lj;
+        rr_inner_pair(kk, s + 1, warp, li, lj);
+        act = lj < k;
+        if (act) {
+          i = sm.lpos[li];
+          j = sm.lpos[lj];
         }
       }
       __syncthreads();
     }
-    if (lane == 0) sm.red_i[warp][1] = my_rot;
+    if (lane == 0) {
+      sm.red_i[warp][1] = my_rot;
+      sm.red_f[warp][2] = my_max;
+    }
     __syncthreads();
     int tot = 0;
-    for (int w = 0; w < PV_WARPS; ++w) tot += sm.red_i[w][1];
+    float dmax = 0.0f;
+    for (int w = 0; w < PV_WARPS; ++w) {
+      tot += sm.red_i[w][1];
+      dmax = fmaxf(dmax, sm.red_f[w][2]);
+    }
     __syncthreads();
     total_rot += tot;
-    if (tot == 0) break;
+    // done when nothing was rotated, or when every rotated pair was already so small that the
+    // next sweep (quadratic convergence: off-diagonals ~ k delta^2) would find nothing above tol_in
+    if (tot == 0 || (float)k * dmax * dmax <= tol_in) break;
   }
   if (inner >= JAC_INNER_MAX_SWEEPS && tid == 0) atomicOr(err, JAC_DEVERR_INNER_LIMIT);
   const long long t_inner = clock64();
