@@ -311,6 +311,8 @@ def main():
                        "fp32_sweeps": info["lowp_sweeps"], "steps_per_sweep": info["steps_per_sweep"],
                        "pivot_phase_share": [c / max(1, sum(info["pivot_cycles"])) for c in info["pivot_cycles"]],
                        "sweep_max_scaled": ["%.2e" % v for v in info["sweep_max_scaled"]],
+                       "inner_sweeps_per_pivot": info["inner_sweeps"] / max(1, info["pivots_rotated"]),
+                       "pivots_rotated": info["pivots_rotated"],
                        "l2": "256 MiB buffer written before each solve, outside the per-solve CUDA events",
                        "parallelism": "replicas" if world > 1 else "single"},
             "e2e": {"value": world * 1000.0 / e2e, "unit": "matrices/s",

@@ -110,6 +110,7 @@ typedef struct {
   long long pivot_cycles[4]; /* SM clocks summed over pivots: statistics, Cholesky, inner sweeps,
                                 J-orthogonalization */
   double sweep_max_scaled[64]; /* per sweep (first 64): max |a_ij| / sqrt(a_ii a_jj) seen */
+  long long inner_sweeps;  /* inner sweeps summed over the transformed pivot blocks */
 } jac_info;
 
 /* Fills *opts with the defaults: w = 32, round-robin, full block, sign-pivoted Cholesky,

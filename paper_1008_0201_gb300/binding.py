@@ -32,7 +32,8 @@ class JacInfo(ctypes.Structure):
                 ("pivots_rotated", ctypes.c_longlong), ("max_scaled_off", ctypes.c_double),
                 ("off_rel", ctypes.c_double), ("launches", ctypes.c_longlong), ("lowp_sweeps", ctypes.c_int),
                 ("global_ns_steps", ctypes.c_int), ("pivot_ns_steps", ctypes.c_longlong),
-                ("pivot_cycles", ctypes.c_longlong * 4), ("sweep_max_scaled", ctypes.c_double * 64)]
+                ("pivot_cycles", ctypes.c_longlong * 4), ("sweep_max_scaled", ctypes.c_double * 64),
+                ("inner_sweeps", ctypes.c_longlong)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("pivot_cycles", "sweep_max_scaled")}

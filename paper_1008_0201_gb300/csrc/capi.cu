@@ -377,7 +377,7 @@ int solve(int m, int n, int dtype, void* Gv, int ldg, const int8_t* Jdev, const 
   }
 
   int sweeps = 0, converged = 0, lowp_sweeps = 0, ns_global = 0;
-  long long rot_total = 0, piv_total = 0, cyc_total[4] = {0, 0, 0, 0}, ns_total = 0;
+  long long rot_total = 0, piv_total = 0, cyc_total[4] = {0, 0, 0, 0}, ns_total = 0, inner_total = 0;
   double prev_max = 1e300;
   SweepRecord hrec = {};
   int last_steps = 0;
@@ -445,6 +445,7 @@ int solve(int m, int n, int dtype, void* Gv, int ldg, const int8_t* Jdev, const 
     rot_total += hrec.rotations;
     piv_total += hrec.pivots_rotated;
     ns_total += hrec.ns_steps;
+    inner_total += hrec.inner_sweeps;
     for (int u = 0; u < 4; ++u) cyc_total[u] += hrec.cyc[u];
     if (hrec.err & JAC_DEVERR_NOTPD) {
       status = JAC_ENOTPD;
@@ -529,6 +530,7 @@ int solve(int m, int n, int dtype, void* Gv, int ldg, const int8_t* Jdev, const 
     info->lowp_sweeps = lowp_sweeps;
     info->global_ns_steps = ns_global;
     info->pivot_ns_steps = ns_total;
+    info->inner_sweeps = inner_total;
     for (int u = 0; u < 4; ++u) info->pivot_cycles[u] = cyc_total[u];
   }
   return status;

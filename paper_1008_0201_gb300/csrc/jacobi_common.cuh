@@ -106,6 +106,7 @@ struct SweepRecord {
   long long pivots_rotated;
   long long cyc[4];
   long long ns_steps;
+  long long inner_sweeps;
   unsigned int err;
   int pad;
 };

@@ -52,6 +52,9 @@ struct PivotSmem {
   int jloc[PV_KM];
   float red_f[PV_WARPS][4];
   int red_i[PV_WARPS][2];
+  float4 rotp[PV_WARPS];      // rotation of pair w in the current inner step: q11, q12, q21, ch-1
+  int rflag[PV_WARPS];
+  float sijv[PV_WARPS];
   int piv;
   int bad;
 };
@@ -232,47 +235,49 @@ __global__ void __launch_bounds__(PV_THREADS, 1)
   if (tid < k) sm.jphys[tid] = sm.jloc[tid];
   __syncthreads();
   const bool signpiv = (pp.factor == 2);
-  const int cx = tid & 63, cy = tid >> 6;  // 2-D map of the trailing update: column cx, rows cy + 16 u
+  // S holds the trailing matrix in its upper triangle: U(a, b) = S[max(a,b) * LDS + min(a,b)]
+  const int cx = tid & 63, cy = tid >> 6;  // trailing update: column cx, rows i + 1 + cy + 16 u <= cx
   for (int i = 0; i < k; ++i) {
     if (signpiv) {
-      // every warp finds the pivot itself (largest unscaled Schur diagonal d_j^2 (1 + s_jj) in the
-      // sign group of step i): a barrier is needed only when a swap follows
-      const int hi = (i < npos) ? npos : k;
-      float best = -1.0f;
-      int bj = i;
-      for (int j = i + lane; j < hi; j += 32) {
-        const float dj = sm.dd[j];
-        const float v = dj * dj * (1.0f + sm.S[j * PV_LDS + j]);
-        if (v > best) {
-          best = v;
-          bj = j;
+      // pivot: the largest unscaled Schur diagonal d_j^2 (1 + s_jj) in the sign group of step i
+      if (warp == 0) {
+        const int hi = (i < npos) ? npos : k;
+        float best = -1.0f;
+        int bj = i;
+        for (int j = i + lane; j < hi; j += 32) {
+          const float dj = sm.dd[j];
+          const float v = dj * dj * (1.0f + sm.S[j * PV_LDS + j]);
+          if (v > best) {
+            best = v;
+            bj = j;
+          }
         }
-      }
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-        const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
-        if (ob > best || (ob == best && oj < bj)) {
-          best = ob;
-          bj = oj;
+        for (int o = 16; o > 0; o >>= 1) {
+          const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+          const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
+          if (ob > best || (ob == best && oj < bj)) {
+            best = ob;
+            bj = oj;
+          }
         }
+        if (lane == 0) sm.piv = bj;
       }
-      const int pv = bj;
-      if (pv != i) {  // uniform: every warp computed the same pv from the same values
-        __syncthreads();  // all warps have read the diagonal before it is permuted
-        // symmetric swap of rows/columns i and pv of the trailing matrix, of the computed rows
-        // of F (columns i and pv), and of the bookkeeping
+      __syncthreads();
+      const int pv = sm.piv;
+      if (pv != i) {  // uniform
+        // symmetric swap of rows/columns i and pv of the trailing matrix (upper storage), of
+        // the computed rows of F (columns i and pv), and of the bookkeeping
         for (int tt = tid; tt < k; tt += PV_THREADS) {
           if (tt > i && tt != pv) {
-            float x = sm.S[i * PV_LDS + tt];
-            sm.S[i * PV_LDS + tt] = sm.S[pv * PV_LDS + tt];
-            sm.S[pv * PV_LDS + tt] = x;
-            x = sm.S[tt * PV_LDS + i];
-            sm.S[tt * PV_LDS + i] = sm.S[tt * PV_LDS + pv];
-            sm.S[tt * PV_LDS + pv] = x;
+            const int a1 = (tt > i) ? tt * PV_LDS + i : i * PV_LDS + tt;
+            const int a2 = (tt > pv) ? tt * PV_LDS + pv : pv * PV_LDS + tt;
+            const float x = sm.S[a1];
+            sm.S[a1] = sm.S[a2];
+            sm.S[a2] = x;
           }
           if (tt < i) {
-            float x = sm.F[i * PV_LDF + tt];
+            const float x = sm.F[i * PV_LDF + tt];
             sm.F[i * PV_LDF + tt] = sm.F[pv * PV_LDF + tt];
             sm.F[pv * PV_LDF + tt] = x;
           }
@@ -308,9 +313,9 @@ __global__ void __launch_bounds__(PV_THREADS, 1)
     if (cy == 0 && cx > i && cx < k) sm.F[cx * PV_LDF + i] = sm.S[cx * PV_LDS + i] / r;
     if (tid == 0) sm.F[i * PV_LDF + i] = sii / (1.0f + r);
     if (cx > i && cx < k) {
-      const float sij = sm.S[cx * PV_LDS + i] * ipiv;
-      for (int ll = i + 1 + cy; ll < k; ll += PV_THREADS / 64)
-        sm.S[ll * PV_LDS + cx] -= sij * sm.S[ll * PV_LDS + i];
+      const float sil = sm.S[cx * PV_LDS + i] * ipiv;
+      for (int jj = i + 1 + cy; jj <= cx; jj += PV_THREADS / 64)
+        sm.S[cx * PV_LDS + jj] -= sil * sm.S[jj * PV_LDS + i];
     }
     __syncthreads();
   }
@@ -342,138 +347,151 @@ __global__ void __launch_bounds__(PV_THREADS, 1)
   const int kk = k + (k & 1);
   float2* F2 = reinterpret_cast<float2*>(sm.F);
   float2* W2 = reinterpret_cast<float2*>(sm.W);
+  // Each inner step runs in three phases separated by barriers:
+  //   A: warp w forms the dot product r_i^T r_j of its pair (shifted: F_i^T F_j);
+  //   B: warp 0, lane l, forms the rotation of pair l from a_ii, a_jj, a_ij: the scalar 2x2
+  //      work of all pairs shares one instruction stream instead of 32 redundant ones;
+  //   C: warp w applies its rotation to the columns of F and W.
   int total_rot = 0, inner = 0;
+  const int P = kk / 2;
   for (inner = 0; inner < JAC_INNER_MAX_SWEEPS; ++inner) {
     // c_i = 2 s_i F_ii + ||f_i||^2 recomputed at the start of every inner sweep, tracked below
     for (int c = warp; c < k; c += PV_WARPS) {
       const float2 f = F2[c * (PV_LDF / 2) + lane];
-      float s = f.x * f.x + f.y * f.y;
-      s = warp_sum(s);
-      if (lane == 0) sm.cn[c] = 2.0f * sm.dd[c] * sm.F[c * PV_LDF + c] + s;
+      float sq = f.x * f.x + f.y * f.y;
+      sq = warp_sum(sq);
+      if (lane == 0) sm.cn[c] = 2.0f * sm.dd[c] * sm.F[c * PV_LDF + c] + sq;
     }
     __syncthreads();
-    int my_rot = 0;
-    float my_max = 0.0f;  // largest scaled |a_ij| rotated by this warp in this sweep
-    // the pair of step 0; the pair of step s + 1 is fetched while step s runs
-    int i = 0, j = 0;
-    bool act = false;
-    if (warp < kk / 2) {
-      int li, lj;
-      rr_inner_pair(kk, 0, warp, li, lj);
-      act = lj < k;
-      if (act) {
-        i = sm.lpos[li];
-        j = sm.lpos[lj];
-      }
-    }
+    int my_rot = 0;       // warp 0, per lane: rotations of pair `lane` in this sweep
+    float my_max = 0.0f;  // largest scaled |a_ij| rotated
     for (int s = 0; s < kk - 1; ++s) {
-      if (act) {
-        const float2 fi = F2[i * (PV_LDF / 2) + lane], fj = F2[j * (PV_LDF / 2) + lane];
-        const float si = sm.dd[i], sj = sm.dd[j];
-        const float Fji = sm.F[i * PV_LDF + j], Fij = sm.F[j * PV_LDF + i];
-        const float ci = sm.cn[i], cj = sm.cn[j];
-        const bool same = sm.jphys[i] == sm.jphys[j];
-        float sij = fi.x * fj.x + fi.y * fj.y;
-        sij = warp_sum(sij);
-        const float aij = si * Fij + sj * Fji + sij;
-        const float aii = fmaf(si, si, ci), ajj = fmaf(sj, sj, cj);
-        const float beta = fabsf(aij);
-        const float scaled = beta * rsqrtf(aii) * rsqrtf(ajj);
-        if (scaled > tol_in) {
-          ++my_rot;
-          my_max = fmaxf(my_max, scaled);
-          const float e = (aij < 0.0f) ? -1.0f : 1.0f;
-          float q11, q12, q21, cm1, dci, dcj;
-          if (same) {
-            // trigonometric, Eq. (2.1): cot(2 phi) = (a_jj - a_ii) / (2 |a_ij|), i.e.
-            // t = sign(a_jj - a_ii) 2|a_ij| / (|a_jj - a_ii| + sqrt((a_jj - a_ii)^2 + 4 |a_ij|^2)),
-            // evaluated after an exact power-of-two scaling of both terms into [1, 4)
-            const float num = (sj - si) * (sj + si) + (cj - ci);
-            const float mxv = fmaxf(fabsf(num), 2.0f * beta);
-            const float sc = __int_as_float(0x7f000000 - (__float_as_int(mxv) & 0x7f800000));
-            const float nu = num * sc, b2 = 2.0f * beta * sc;
-            const float den = fabsf(nu) + sqrtf(fmaf(nu, nu, b2 * b2));
-            const float t = copysignf(__fdividef(b2, den), num);
-            const float c = rsqrtf(fmaf(t, t, 1.0f));
-            const float s_ = t * c;
-            cm1 = -__fdividef(s_ * s_, 1.0f + c);  // c - 1
-            q11 = c;
-            q12 = e * s_;
-            q21 = -e * s_;
-            dci = -t * beta;  // a_ii' = a_ii - t |a_ij|, a_jj' = a_jj + t |a_ij|
-            dcj = t * beta;
-          } else {
-            // hyperbolic: coth(2 phi) = -(a_ii + a_jj) / (2 |a_ij|), i.e.
-            // t = -2|a_ij| / (a_ii + a_jj + sqrt((a_ii + a_jj - 2|a_ij|)(a_ii + a_jj + 2|a_ij|))),
-            // with the |tanh| < 1 guard of Sec. 3.2
-            const float apd = aii + ajj;
-            const float sc = __int_as_float(0x7f000000 - (__float_as_int(apd) & 0x7f800000));
-            const float ap = apd * sc, b2 = 2.0f * beta * sc;
-            const float r2 = (ap - b2) * (ap + b2);
-            float t = (r2 > 0.0f) ? -__fdividef(b2, ap + sqrtf(r2)) : -1.0f;
-            if (!(fabsf(t) < 1.0f) || !((1.0f - t) * (1.0f + t) > 0.0f)) t = copysignf(0.9f, t);
-            const float ch = rsqrtf((1.0f - t) * (1.0f + t));
-            const float sh = t * ch;
-            cm1 = __fdividef(sh * sh, 1.0f + ch);  // ch - 1
-            q11 = ch;
-            q12 = e * sh;
-            q21 = e * sh;
-            dci = t * beta;  // both diagonals move by t |a_ij| (the J-trace is invariant)
-            dcj = t * beta;
-          }
-          const float2 Q11 = make_float2(q11, q11), Q12 = make_float2(q12, q12), Q21 = make_float2(q21, q21);
-          float2 nfi = fma2(Q11, fi, mul2(Q21, fj));
-          float2 nfj = fma2(Q11, fj, mul2(Q12, fi));
-          // + Dp (Q - I): column i gets si (q11-1) at row i and sj q21 at row j; column j
-          // gets si q12 at row i and sj (q22-1) at row j
-          if (lane == (i >> 1)) {
-            if (i & 1) { nfi.y += si * cm1; nfj.y += si * q12; } else { nfi.x += si * cm1; nfj.x += si * q12; }
-          }
-          if (lane == (j >> 1)) {
-            if (j & 1) { nfi.y += sj * q21; nfj.y += sj * cm1; } else { nfi.x += sj * q21; nfj.x += sj * cm1; }
-          }
-          F2[i * (PV_LDF / 2) + lane] = nfi;
-          F2[j * (PV_LDF / 2) + lane] = nfj;
-          const float2 wi = W2[i * (PV_LDF / 2) + lane], wj = W2[j * (PV_LDF / 2) + lane];
-          float2 nwi = fma2(Q11, wi, mul2(Q21, wj));
-          float2 nwj = fma2(Q11, wj, mul2(Q12, wi));
-          if (lane == (i >> 1)) {
-            if (i & 1) { nwi.y += cm1; nwj.y += q12; } else { nwi.x += cm1; nwj.x += q12; }
-          }
-          if (lane == (j >> 1)) {
-            if (j & 1) { nwi.y += q21; nwj.y += cm1; } else { nwi.x += q21; nwj.x += cm1; }
-          }
-          W2[i * (PV_LDF / 2) + lane] = nwi;
-          W2[j * (PV_LDF / 2) + lane] = nwj;
-          if (lane == 0) {
-            sm.cn[i] = ci + dci;
-            sm.cn[j] = cj + dcj;
-          }
-        }
-      }
-      // next step's pair (lpos is constant during the inner sweeps)
-      if (warp < kk / 2 && s + 1 < kk - 1) {
+      // ---- A
+      int i = 0, j = 0;
+      bool act = false;
+      float2 fi = make_float2(0.f, 0.f), fj = make_float2(0.f, 0.f);
+      if (warp < P) {
         int li, lj;
-        rr_inner_pair(kk, s + 1, warp, li, lj);
+        rr_inner_pair(kk, s, warp, li, lj);
         act = lj < k;
         if (act) {
           i = sm.lpos[li];
           j = sm.lpos[lj];
+          fi = F2[i * (PV_LDF / 2) + lane];
+          fj = F2[j * (PV_LDF / 2) + lane];
+          float sij = fi.x * fj.x + fi.y * fj.y;
+          sij = warp_sum(sij);
+          if (lane == 0) sm.sijv[warp] = sij;
         }
       }
       __syncthreads();
+      // ---- B
+      if (warp == 0) {
+        int rot = 0;
+        float4 rp = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (lane < P) {
+          int li, lj;
+          rr_inner_pair(kk, s, lane, li, lj);
+          if (lj < k) {
+            const int bi = sm.lpos[li], bj = sm.lpos[lj];
+            const float si = sm.dd[bi], sj = sm.dd[bj];
+            const float ci = sm.cn[bi], cj = sm.cn[bj];
+            const float aij = si * sm.F[bj * PV_LDF + bi] + sj * sm.F[bi * PV_LDF + bj] + sm.sijv[lane];
+            const float aii = fmaf(si, si, ci), ajj = fmaf(sj, sj, cj);
+            const float beta = fabsf(aij);
+            const float scaled = beta * rsqrtf(aii) * rsqrtf(ajj);
+            if (scaled > tol_in) {
+              rot = 1;
+              ++my_rot;
+              my_max = fmaxf(my_max, scaled);
+              const float e = (aij < 0.0f) ? -1.0f : 1.0f;
+              float dci, dcj;
+              if (sm.jphys[bi] == sm.jphys[bj]) {
+                // trigonometric, Eq. (2.1): cot(2 phi) = (a_jj - a_ii) / (2 |a_ij|), i.e.
+                // t = sign(a_jj - a_ii) 2|a_ij| / (|a_jj - a_ii| + sqrt((a_jj - a_ii)^2 + 4|a_ij|^2)),
+                // evaluated after an exact power-of-two scaling of both terms into [1, 4)
+                const float num = (sj - si) * (sj + si) + (cj - ci);
+                const float mxv = fmaxf(fabsf(num), 2.0f * beta);
+                const float sc = __int_as_float(0x7f000000 - (__float_as_int(mxv) & 0x7f800000));
+                const float nu = num * sc, b2 = 2.0f * beta * sc;
+                const float den = fabsf(nu) + sqrtf(fmaf(nu, nu, b2 * b2));
+                const float t = copysignf(__fdividef(b2, den), num);
+                const float c = rsqrtf(fmaf(t, t, 1.0f));
+                const float s_ = t * c;
+                rp = make_float4(c, e * s_, -e * s_, -__fdividef(s_ * s_, 1.0f + c));
+                dci = -t * beta;  // a_ii' = a_ii - t |a_ij|, a_jj' = a_jj + t |a_ij|
+                dcj = t * beta;
+              } else {
+                // hyperbolic: coth(2 phi) = -(a_ii + a_jj) / (2 |a_ij|), i.e.
+                // t = -2|a_ij| / (a_ii + a_jj + sqrt((a_ii + a_jj - 2|a_ij|)(a_ii + a_jj + 2|a_ij|))),
+                // with the |tanh| < 1 guard of Sec. 3.2
+                const float apd = aii + ajj;
+                const float sc = __int_as_float(0x7f000000 - (__float_as_int(apd) & 0x7f800000));
+                const float ap = apd * sc, b2 = 2.0f * beta * sc;
+                const float r2 = (ap - b2) * (ap + b2);
+                float t = (r2 > 0.0f) ? -__fdividef(b2, ap + sqrtf(r2)) : -1.0f;
+                if (!(fabsf(t) < 1.0f) || !((1.0f - t) * (1.0f + t) > 0.0f)) t = copysignf(0.9f, t);
+                const float ch = rsqrtf((1.0f - t) * (1.0f + t));
+                const float sh = t * ch;
+                rp = make_float4(ch, e * sh, e * sh, __fdividef(sh * sh, 1.0f + ch));
+                dci = t * beta;  // both diagonals move by t |a_ij| (the J-trace is invariant)
+                dcj = t * beta;
+              }
+              sm.cn[bi] = ci + dci;
+              sm.cn[bj] = cj + dcj;
+            }
+          }
+          sm.rotp[lane] = rp;
+          sm.rflag[lane] = rot;
+        }
+      }
+      __syncthreads();
+      // ---- C
+      if (act && sm.rflag[warp]) {
+        const float4 rp = sm.rotp[warp];
+        const float q11 = rp.x, q12 = rp.y, q21 = rp.z, cm1 = rp.w;
+        const float si = sm.dd[i], sj = sm.dd[j];
+        const float2 Q11 = make_float2(q11, q11), Q12 = make_float2(q12, q12), Q21 = make_float2(q21, q21);
+        float2 nfi = fma2(Q11, fi, mul2(Q21, fj));
+        float2 nfj = fma2(Q11, fj, mul2(Q12, fi));
+        // + Dp (Q - I): column i gets si (q11-1) at row i and sj q21 at row j; column j
+        // gets si q12 at row i and sj (q22-1) at row j
+        if (lane == (i >> 1)) {
+          if (i & 1) { nfi.y += si * cm1; nfj.y += si * q12; } else { nfi.x += si * cm1; nfj.x += si * q12; }
+        }
+        if (lane == (j >> 1)) {
+          if (j & 1) { nfi.y += sj * q21; nfj.y += sj * cm1; } else { nfi.x += sj * q21; nfj.x += sj * cm1; }
+        }
+        F2[i * (PV_LDF / 2) + lane] = nfi;
+        F2[j * (PV_LDF / 2) + lane] = nfj;
+        const float2 wi = W2[i * (PV_LDF / 2) + lane], wj = W2[j * (PV_LDF / 2) + lane];
+        float2 nwi = fma2(Q11, wi, mul2(Q21, wj));
+        float2 nwj = fma2(Q11, wj, mul2(Q12, wi));
+        if (lane == (i >> 1)) {
+          if (i & 1) { nwi.y += cm1; nwj.y += q12; } else { nwi.x += cm1; nwj.x += q12; }
+        }
+        if (lane == (j >> 1)) {
+          if (j & 1) { nwi.y += q21; nwj.y += cm1; } else { nwi.x += q21; nwj.x += cm1; }
+        }
+        W2[i * (PV_LDF / 2) + lane] = nwi;
+        W2[j * (PV_LDF / 2) + lane] = nwj;
+      }
+      __syncthreads();
     }
-    if (lane == 0) {
-      sm.red_i[warp][1] = my_rot;
-      sm.red_f[warp][2] = my_max;
-    }
-    __syncthreads();
     int tot = 0;
     float dmax = 0.0f;
-    for (int w = 0; w < PV_WARPS; ++w) {
-      tot += sm.red_i[w][1];
-      dmax = fmaxf(dmax, sm.red_f[w][2]);
+    if (warp == 0) {
+      tot = warp_sum_i(my_rot);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) my_max = fmaxf(my_max, __shfl_xor_sync(0xffffffffu, my_max, o));
+      if (lane == 0) {
+        sm.red_i[0][1] = tot;
+        sm.red_f[0][2] = my_max;
+      }
     }
+    __syncthreads();
+    tot = sm.red_i[0][1];
+    dmax = sm.red_f[0][2];
     __syncthreads();
     total_rot += tot;
     // done when nothing was rotated, or when every rotated pair was already so small that the

@@ -17,9 +17,9 @@ namespace jac {
 __global__ void k_sweep_reduce(const PairStat* __restrict__ stats, const int* __restrict__ counts, int nsteps,
                                int half, int nb, const unsigned* __restrict__ err, SweepRecord* __restrict__ rec) {
   __shared__ double sm_d[8][3];
-  __shared__ long long sm_l[8][7];
+  __shared__ long long sm_l[8][8];
   double mx = 0.0, off2 = 0.0, tr = 0.0;
-  long long rot = 0, piv = 0, cy[4] = {0, 0, 0, 0}, ns = 0;
+  long long rot = 0, piv = 0, cy[4] = {0, 0, 0, 0}, ns = 0, isw = 0;
   const double wdiag = 1.0 / (double)(nb > 1 ? nb - 1 : 1);
   for (int e = threadIdx.x; e < nsteps * half; e += blockDim.x) {
     const int s = e / half, slot = e % half;
@@ -31,6 +31,7 @@ __global__ void k_sweep_reduce(const PairStat* __restrict__ stats, const int* __
     rot += st.rotations;
     piv += st.active;
     ns += st.ns_steps;
+    isw += st.inner_sweeps;
     for (int u = 0; u < 4; ++u) cy[u] += st.cyc[u];
   }
   mx = warp_max_d(mx);
@@ -41,6 +42,7 @@ __global__ void k_sweep_reduce(const PairStat* __restrict__ stats, const int* __
     rot += __shfl_xor_sync(0xffffffffu, rot, o);
     piv += __shfl_xor_sync(0xffffffffu, piv, o);
     ns += __shfl_xor_sync(0xffffffffu, ns, o);
+    isw += __shfl_xor_sync(0xffffffffu, isw, o);
     for (int u = 0; u < 4; ++u) cy[u] += __shfl_xor_sync(0xffffffffu, cy[u], o);
   }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -51,6 +53,7 @@ __global__ void k_sweep_reduce(const PairStat* __restrict__ stats, const int* __
     sm_l[warp][0] = rot;
     sm_l[warp][1] = piv;
     sm_l[warp][2] = ns;
+    sm_l[warp][7] = isw;
     for (int u = 0; u < 4; ++u) sm_l[warp][3 + u] = cy[u];
   }
   __syncthreads();
@@ -63,6 +66,7 @@ __global__ void k_sweep_reduce(const PairStat* __restrict__ stats, const int* __
       r.rotations += sm_l[w][0];
       r.pivots_rotated += sm_l[w][1];
       r.ns_steps += sm_l[w][2];
+      r.inner_sweeps += sm_l[w][7];
       for (int u = 0; u < 4; ++u) r.cyc[u] += sm_l[w][3 + u];
     }
     r.err = *err;
