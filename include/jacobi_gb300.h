@@ -172,6 +172,28 @@ int jacobi_eig_pd(int m, int n, int dtype, void* G, int ldg, const jac_opts* opt
 int jacobi_sched_pairs(int nb, int ordering, const double* weights, int* pairs, int* counts,
                        int max_steps, int* nsteps, jac_stream_t stream);
 
+/* Largest block count accepted by jacobi_sched_pairs_noalloc. */
+#define JAC_NOALLOC_MAX_NB 256
+
+/*
+ * jacobi_sched_pairs_noalloc -- jacobi_sched_pairs for callers that cannot allocate device
+ * memory (no counterpart in the paper).  Same arguments, outputs and return codes as
+ * jacobi_sched_pairs, but it calls no cudaMalloc / cudaMallocAsync / cudaFree and no allocating
+ * library routine: the scratch of the per-cycle weight ordering (the ranked pair list and the
+ * step count) is a fixed array of about 128 KiB inside the library, which every device that
+ * loads the library holds until the process exits.  Meant for callers whose device memory is
+ * owned by an external pool, that run under a fixed memory budget, or that must not take the
+ * allocator's locks or its implicit synchronization.
+ *  - nb above JAC_NOALLOC_MAX_NB (256) is rejected with -1 before any work is queued.
+ *  - The first call on a device resolves the array's device address (cudaGetSymbolAddress)
+ *    with that device current; make that first call before any stream capture.
+ *  - All calls share the one array, which keeps the last call's contents (the step count is
+ *    cleared at the start of every call): calls that overlap on the GPU, on different streams
+ *    or from different host threads, race on it and must be serialized by the caller.
+ */
+int jacobi_sched_pairs_noalloc(int nb, int ordering, const double* weights, int* pairs, int* counts,
+                               int max_steps, int* nsteps, jac_stream_t stream);
+
 /* Kernels that the timing hooks below can bracket. */
 enum jac_kernel { JAC_KERNEL_GRAM = 0, JAC_KERNEL_PIVOT = 1, JAC_KERNEL_UPDATE = 2, JAC_KERNEL_COUNT = 3 };
 

@@ -52,7 +52,8 @@ class JacobiError(RuntimeError):
 _lib = None
 
 EXPORTS = ("jacobi_default_opts", "jacobi_status_string", "jacobi_version", "jacobi_hsvd", "jacobi_eig_pd",
-           "jacobi_sched_pairs", "jacobi_profile_begin", "jacobi_profile_read", "jacobi_profile_end")
+           "jacobi_sched_pairs", "jacobi_profile_begin", "jacobi_profile_read", "jacobi_profile_end",
+           "jacobi_sched_pairs_noalloc")
 KERNEL = {"gram": 0, "pivot": 1, "update": 2}
 
 
@@ -78,6 +79,8 @@ def load_library(path=LIB_PATH):
     lib.jacobi_eig_pd.restype = I
     lib.jacobi_sched_pairs.argtypes = [I, I, P, P, P, I, ctypes.POINTER(ctypes.c_int), P]
     lib.jacobi_sched_pairs.restype = I
+    lib.jacobi_sched_pairs_noalloc.argtypes = [I, I, P, P, P, I, ctypes.POINTER(ctypes.c_int), P]
+    lib.jacobi_sched_pairs_noalloc.restype = I
     lib.jacobi_profile_begin.argtypes = [I]
     lib.jacobi_profile_begin.restype = I
     lib.jacobi_profile_read.argtypes = [I, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong)]
@@ -173,8 +176,9 @@ def jacobi_hsvd_raw(m, n, G_ptr, ldg, J_ptr, opts, lam_ptr, U_ptr, ldu, V_ptr, l
     return rc, info.as_dict()
 
 
-def jacobi_sched_pairs(nb, ordering, weights=None, device="cuda", max_steps=None):
-    """Device scheduler: list of (count, 2) int tensors, one per step of a cycle."""
+def jacobi_sched_pairs(nb, ordering, weights=None, device="cuda", max_steps=None, noalloc=False):
+    """Device scheduler: list of (count, 2) int tensors, one per step of a cycle.  noalloc=True
+    calls jacobi_sched_pairs_noalloc (library-resident scratch, no device allocation)."""
     lib = load_library()
     if isinstance(ordering, str):
         ordering = ORDER[ordering]
@@ -187,11 +191,12 @@ def jacobi_sched_pairs(nb, ordering, weights=None, device="cuda", max_steps=None
     if weights is not None:
         w = weights.to(device=device, dtype=torch.float64).contiguous()
     ns = ctypes.c_int(0)
-    rc = lib.jacobi_sched_pairs(nb, ordering, ctypes.c_void_p(w.data_ptr()) if w is not None else None,
+    fn = lib.jacobi_sched_pairs_noalloc if noalloc else lib.jacobi_sched_pairs
+    rc = fn(nb, ordering, ctypes.c_void_p(w.data_ptr()) if w is not None else None,
                                 ctypes.c_void_p(pairs.data_ptr()), ctypes.c_void_p(counts.data_ptr()), max_steps,
                                 ctypes.byref(ns), _stream(torch.device(device)))
     if rc != JAC_OK:
-        raise JacobiError(rc, "jacobi_sched_pairs failed")
+        raise JacobiError(rc, "jacobi_sched_pairs%s failed" % ("_noalloc" if noalloc else ""))
     tab = pairs.view(max_steps, half, 2).cpu()
     cnt = counts.cpu()
     return [tab[s, : int(cnt[s])].clone() for s in range(ns.value)]
