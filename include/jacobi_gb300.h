@@ -73,13 +73,16 @@ enum jac_factor {
   JAC_FACTOR_CHOL_SIGNPIV = 2 /* J_P-sign-pivoted Cholesky, Algorithm 3.3 (HFSC) */
 };
 
-/* Arithmetic of the sweeps (both modes return FP64-accurate results). */
+/* Arithmetic of the sweeps (FP64 and FP32 return FP64-accurate results). */
 enum jac_precision {
   JAC_PREC_FP64 = 0, /* every sweep: Gram, update and J-orthogonalization of V_P in FP64 (mma f64) */
-  JAC_PREC_FP32 = 1  /* sweeps on an FP32 copy of G with FP32 Gram/update products until the scaled
+  JAC_PREC_FP32 = 1, /* sweeps on an FP32 copy of G with FP32 Gram/update products until the scaled
                         off-norm reaches what FP32 resolves, then V is made J-unitary in FP64,
                         G = G_in V, and FP64 sweeps polish to tol (the outer iteration is
-                        self-correcting, Sec. 4) */
+                        self-correcting, Sec. 4).  jacobi_hsvd / jacobi_eig_pd only. */
+  JAC_PREC_FP32_ONLY = 2 /* every sweep on the FP32 copy, no FP64 polish: results accurate to
+                            FP32 (eps = 2^-24); tol <= 0 selects max(n, 8 sqrt(m)) * 2^-24, the
+                            smallest scaled off-diagonal an FP32 Gram of m rows resolves */
 };
 
 typedef struct {
@@ -128,7 +131,7 @@ int jacobi_version(void);
  * Sec. 3.2, Algorithm 3.4 (full block; Cholesky per opts->factor, Algorithm 3.3).
  *
  *  1 m, 2 n        G is m x n, m >= n >= 1 (full column rank required when J != I).
- *  3 dtype         JAC_R64 or JAC_C128.
+ *  3 dtype         JAC_R64 (JAC_C128 is rejected with -3 in this version).
  *  4 G, 5 ldg      device, in/out.  On return G = G_in V: the unnormalized U Sigma, columns in
  *                  output order.
  *  6 J             device int8[n], entries +1 / -1, any order (sorted internally to
@@ -153,6 +156,39 @@ int jacobi_hsvd(int m, int n, int dtype, void* G, int ldg, const int8_t* J, cons
  */
 int jacobi_eig_pd(int m, int n, int dtype, void* G, int ldg, const jac_opts* opts, double* lambda,
                   void* U, int ldu, void* V, int ldv, jac_info* info, jac_stream_t stream);
+
+/*
+ * jacobi_eig_batched -- many independent problems of uneven order in one call: the same sweep
+ * (Algorithm 3.4, Sec. 3.2) of every problem runs in the same kernel launches, each problem taking
+ * its pivot pairs from the grid, and a problem leaves the launches when one of its sweeps rotates
+ * nothing.  Problem b is jacobi_hsvd(m[b], n[b], dtype, G[b], ldg[b], J[b], opts, lambda[b],
+ * U[b], ldu[b], V[b], ldv[b], &info[b]) except that opts->block_w is ignored: the block width
+ * is chosen per size class (one pivot block of the whole problem for n <= 64, blocks of 32
+ * columns above).
+ *  1 batch         >= 0 problems (0: nothing is done).
+ *  2 m, 3 n        host int[batch]; 1 <= n[b] <= m[b], n[b] <= 128 in this version.
+ *  4 dtype         JAC_R64.
+ *  5 G, 6 ldg      host arrays of device pointers / leading dimensions, as jacobi_hsvd.
+ *  7 J             host array of device int8 pointers; NULL (the array) means J = I for every
+ *                  problem, a NULL entry J = I for that problem.  Entries other than +-1 fail
+ *                  that problem with info[b].status = -7.
+ *  8 opts          host, as jacobi_hsvd; ordering JAC_ORDER_CYCLE_WEIGHT and precision
+ *                  JAC_PREC_FP32 are rejected (-8); JAC_PREC_FP32_ONLY is the FP32 variant.
+ *  9 lambda        host array of device double pointers, lambda[b] of n[b] entries.
+ * 10 U, 11 ldu     host arrays or NULL; a NULL entry skips U for that problem; U[b] != G[b].
+ * 12 V, 13 ldv     host arrays, required iff opts->want_v.
+ * 14 info          host jac_info[batch] or NULL: per problem sweeps, converged, status,
+ *                  rotations, steps_per_sweep; info[0].launches counts the launches of the call.
+ * 15 stream        CUDA stream.
+ * Returns a negative argument position, a call-wide error (JAC_ECUDA, JAC_ENOMEM), or else the
+ * first non-zero per-problem status in input order (0 when every problem converged).  Failing
+ * problems do not stop the others; a problem that fails validation or a pivot leaves its G and
+ * outputs unwritten.  Blocks the host until the batch is done.
+ */
+int jacobi_eig_batched(int batch, const int* m, const int* n, int dtype, void* const* G,
+                       const int* ldg, const int8_t* const* J, const jac_opts* opts,
+                       double* const* lambda, void* const* U, const int* ldu, void* const* V,
+                       const int* ldv, jac_info* info, jac_stream_t stream);
 
 /*
  * jacobi_sched_pairs -- the device scheduler on its own (Sec. 2.4), for inspection and tests.

@@ -17,7 +17,7 @@ JAC_OK, JAC_ENOTCONV, JAC_ENOTPD, JAC_ENONFINITE, JAC_ECUDA, JAC_ENOMEM, JAC_EIN
 JAC_R64, JAC_C128 = 0, 1
 ORDER = {"modulus": 0, "modulus_mod": 1, "round_robin": 2, "cycle_weight": 3}
 FACTOR = {"chol": 0, "chol_signpiv": 2}
-PRECISION = {"fp64": 0, "fp32": 1}
+PRECISION = {"fp64": 0, "fp32": 1, "fp32_only": 2}
 
 
 class JacOpts(ctypes.Structure):
@@ -53,7 +53,7 @@ _lib = None
 
 EXPORTS = ("jacobi_default_opts", "jacobi_status_string", "jacobi_version", "jacobi_hsvd", "jacobi_eig_pd",
            "jacobi_sched_pairs", "jacobi_profile_begin", "jacobi_profile_read", "jacobi_profile_end",
-           "jacobi_sched_pairs_noalloc")
+           "jacobi_sched_pairs_noalloc", "jacobi_eig_batched")
 KERNEL = {"gram": 0, "pivot": 1, "update": 2}
 
 
@@ -79,6 +79,8 @@ def load_library(path=LIB_PATH):
     lib.jacobi_eig_pd.restype = I
     lib.jacobi_sched_pairs.argtypes = [I, I, P, P, P, I, ctypes.POINTER(ctypes.c_int), P]
     lib.jacobi_sched_pairs.restype = I
+    lib.jacobi_eig_batched.argtypes = [I, P, P, I, P, P, P, ctypes.POINTER(JacOpts), P, P, P, P, P, P, P]
+    lib.jacobi_eig_batched.restype = I
     lib.jacobi_sched_pairs_noalloc.argtypes = [I, I, P, P, P, I, ctypes.POINTER(ctypes.c_int), P]
     lib.jacobi_sched_pairs_noalloc.restype = I
     lib.jacobi_profile_begin.argtypes = [I]
@@ -174,6 +176,84 @@ def jacobi_hsvd_raw(m, n, G_ptr, ldg, J_ptr, opts, lam_ptr, U_ptr, ldu, V_ptr, l
                          ctypes.c_void_p(V_ptr) if V_ptr else None, ldv, ctypes.byref(info),
                          ctypes.c_void_p(stream_ptr))
     return rc, info.as_dict()
+
+
+def jacobi_eig_batched_raw(m, n, G_ptrs, ldg, J_ptrs, opts, lam_ptrs, U_ptrs, ldu, V_ptrs, ldv, stream_ptr,
+                           want_info=True):
+    """Pointer-level batched call.  m, n, ldg, ldu, ldv: int32 numpy arrays; *_ptrs: uint64 numpy
+    arrays of device addresses (J_ptrs / U_ptrs / V_ptrs may be None).  Returns (status, infos)
+    with infos a JacInfo array (or None)."""
+    import numpy as np
+
+    lib = load_library()
+    batch = len(m)
+
+    def arr(a, dt):
+        if a is None:
+            return None, None
+        a = np.ascontiguousarray(a, dtype=dt)
+        return a, ctypes.c_void_p(a.ctypes.data)
+
+    keep = []
+    cargs = []
+    for a, dt in ((m, np.int32), (n, np.int32)):
+        k, c = arr(a, dt)
+        keep.append(k)
+        cargs.append(c)
+    gk, gc = arr(G_ptrs, np.uint64)
+    lk, lc = arr(ldg, np.int32)
+    jk, jc = arr(J_ptrs, np.uint64)
+    lak, lac = arr(lam_ptrs, np.uint64)
+    uk, uc = arr(U_ptrs, np.uint64)
+    luk, luc = arr(ldu, np.int32)
+    vk, vc = arr(V_ptrs, np.uint64)
+    lvk, lvc = arr(ldv, np.int32)
+    keep += [gk, lk, jk, lak, uk, luk, vk, lvk]
+    infos = (JacInfo * batch)() if want_info and batch > 0 else None
+    rc = lib.jacobi_eig_batched(batch, cargs[0], cargs[1], JAC_R64, gc, lc, jc, ctypes.byref(opts), lac, uc, luc, vc,
+                                lvc, infos, ctypes.c_void_p(stream_ptr))
+    del keep
+    return rc, infos
+
+
+def jacobi_eig_batched(Gs, Js=None, opts=None, want_u=False, raise_on_error=True):
+    # raise_on_error=False returns the per-problem statuses in info["status"] (argument and
+    # call-wide errors raise regardless)
+    """Batched solve of independent problems of uneven order (one call, shared launches).
+    Gs: list of (m_b, n_b) CUDA tensors on one device; Js: None (every H positive definite) or a
+    list whose entries are (n_b,) +-1 tensors or None (J = I for that problem).  opts.block_w is
+    ignored (chosen per size class).  Returns (list of dict(lam, G, U, V, info), status)."""
+    import numpy as np
+
+    if opts is None:
+        opts = default_opts()
+    batch = len(Gs)
+    if batch == 0:
+        return [], JAC_OK
+    dev = Gs[0].device
+    for i, G in enumerate(Gs):
+        _check_cuda(G, "Gs[%d]" % i)
+    Gts = [_colmajor(G) for G in Gs]
+    ms = np.array([G.shape[0] for G in Gs], dtype=np.int32)
+    ns = np.array([G.shape[1] for G in Gs], dtype=np.int32)
+    lams = [torch.empty(int(k), dtype=torch.float64, device=dev) for k in ns]
+    Uts = [torch.empty((int(k), int(mm)), dtype=torch.float64, device=dev) for mm, k in zip(ms, ns)] if want_u else None
+    Vts = [torch.empty((int(k), int(k)), dtype=torch.float64, device=dev) for k in ns] if opts.want_v else None
+    Jds = None
+    if Js is not None:
+        Jds = [None if J is None else J.to(device=dev, dtype=torch.int8).contiguous() for J in Js]
+    ptr = lambda ts: np.array([0 if t is None else t.data_ptr() for t in ts], dtype=np.uint64)
+    rc, infos = jacobi_eig_batched_raw(
+        ms, ns, ptr(Gts), ms, ptr(Jds) if Jds is not None else None, opts, ptr(lams),
+        ptr(Uts) if Uts is not None else None, ms if Uts is not None else None,
+        ptr(Vts) if Vts is not None else None, ns if Vts is not None else None, _stream(dev).value or 0)
+    if rc < 0 or rc in (JAC_ECUDA, JAC_ENOMEM) or (rc != JAC_OK and raise_on_error):
+        raise JacobiError(rc, status_string(rc))
+    outs = []
+    for i in range(batch):
+        outs.append(dict(lam=lams[i], G=Gts[i].t(), U=Uts[i].t() if Uts is not None else None,
+                         V=Vts[i].t() if Vts is not None else None, info=infos[i].as_dict()))
+    return outs, rc
 
 
 def jacobi_sched_pairs(nb, ordering, weights=None, device="cuda", max_steps=None, noalloc=False):

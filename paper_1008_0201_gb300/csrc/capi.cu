@@ -1,14 +1,16 @@
 // capi.cu -- host driver of the sweep loop and the C ABI declared in include/jacobi_gb300.h.
 //
-// The driver does no numerics on the host: it validates arguments, sorts J into
-// diag(I, -I) (Algorithms 3.2 / 3.4 assume that order), lays out the block partition
-// (Sec. 3: widths differ by at most one), launches the device scheduler, and then per sweep
-// the step kernels gram -> pivot -> update for every step, followed by the sweep reduction,
-// whose small record is the only value read back per sweep.
+// The driver does no numerics on the host.  It validates arguments, lays out the block
+// partition (Sec. 3: widths differ by at most one), builds one descriptor per problem (a single
+// solve is a batch of one) and launches, per sweep, the step kernels gram -> pivot -> update for
+// every step of the ordering, then the sweep reduction.  The only values read back per sweep
+// are one small record (single solve) or the number of problems still active (batch).
 #include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <vector>
 
@@ -20,33 +22,33 @@ __global__ void k_sched_static(int nb, int ordering, int nsteps, int* pairs, int
 __global__ void k_sched_cycle_weight(int nb, const double* w, int* order_g, int* pairs, int* counts, int max_steps,
                                      int* nsteps_out);
 __global__ void k_block_weights32(const float* G32, int mp, int nb, const int* boff, double* w);
-__global__ void k_gram32(JacStepArgs a, const float* G32, const int* step_pairs, const int* step_count, int CS,
-                         double* Ap);
-__global__ void k_update32(JacStepArgs a, float* G32, float* V32, const int* step_pairs, const int* step_count,
-                           const double* vp, const int* skip, int gslabs);
+__global__ void k_gram(const JacProb* probs, int s, int CS);
+__global__ void k_update(const JacProb* probs, int s, int gslabs);
+__global__ void k_gram32(const JacProb* probs, int s, int CS);
+__global__ void k_update32(const JacProb* probs, int s, int gslabs);
+int pivot_set_attributes();
+void pivot_launch(int km, int max_half, int nprob, cudaStream_t st, const JacProb* probs, int s, const PivotParams& pp);
+int pivot64_set_attributes();
+void pivot64_launch(int km, int max_half, int nprob, cudaStream_t st, const JacProb* probs, int s,
+                    const PivotParams& pp);
+__global__ void k_sweep_reduce(JacProb* probs, JacIO* io, SweepRecord* rec, int deactivate, int* remaining);
+__global__ void k_sort_signs(const JacProb* probs, JacIO* io, int8_t* Js_all, const long long* js_off);
+__global__ void k_apply_flags(JacProb* probs, const JacIO* io, int nprob);
+__global__ void k_gather_in(const JacProb* probs, const JacIO* io);
+__global__ void k_init_v(const JacProb* probs, const JacIO* io);
+__global__ void k_check_finite(const JacProb* probs, JacIO* io);
+__global__ void k_colnorm(const JacProb* probs, const JacIO* io);
+__global__ void k_rank(const JacProb* probs, const JacIO* io);
+__global__ void k_scatter(const JacProb* probs, const JacIO* io);
 __global__ void k_gemm64(int Mr, int Nc, int K, const double* A, int lda, int transA, const double* B, int ldb,
-                         const int8_t* sb, const int8_t* dsub, double* C, int ldc, int sym);
+                         const int8_t* sb, const int8_t* dsub, double* C, int ldc, int sym, int transB, long long sa,
+                         long long sbb, long long sc);
 __global__ void k_ns_correct(int Mr, int Nc, int K, const float* Af, int lda, const float* Bf, int ldb, double* V,
                              int ldv);
 __global__ void k_cvt64to32(int rows, int cols, const double* src, int lds, float* dst, int ldd, const int8_t* rsign);
 __global__ void k_cvt32to64(int rows, int cols, const float* src, int lds, double* dst, int ldd);
 __global__ void k_absmax64(int n, const double* M, int ldm, unsigned long long* out);
-__global__ void k_gram(JacStepArgs a, const int* step_pairs, const int* step_count, int CS, double* Ap);
-__global__ void k_update(JacStepArgs a, const int* step_pairs, const int* step_count, const double* vp,
-                         const int* skip, int gslabs);
-__global__ void k_pivot(JacStepArgs a, const int* step_pairs, const int* step_count, const double* Ap,
-                        PivotParams pp, double* vp, int* skip, PairStat* stats, unsigned* err);
-__global__ void k_sweep_reduce(const PairStat* stats, const int* counts, int nsteps, int half, int nb,
-                               const unsigned* err, SweepRecord* rec);
-__global__ void k_gather_in(const double* G, int ldg, int m, int mp, const int* perm_in, double* Gw);
-__global__ void k_init_v(int n, int np, const int* perm_in, double* Vw);
-__global__ void k_check_finite(const double* G, int ldg, int m, int n, unsigned* err);
-__global__ void k_colnorm(const double* Gw, int mp, int n, const int8_t* Js, double* nrm2, double* lam);
-__global__ void k_rank(const double* lam, int n, int* rank);
-__global__ void k_scatter(const double* Gw, int mp, int m, const double* Vw, int np, int n, const double* nrm2,
-                          const double* lam, const int* rank, double* lambda, double* G, int ldg, double* U,
-                          int ldu, double* V, int ldv);
-size_t pivot_smem_bytes();
+__global__ void k_lowp_copy(const JacProb* probs, int to64);
 }  // namespace jac
 
 using namespace jac;
@@ -84,7 +86,6 @@ struct ProfRun {
     if (!e && cudaEventCreate(&e) != cudaSuccess) e = nullptr;
     return e;
   }
-  // record before / after one launch of kernel k
   size_t pre(int k, cudaStream_t st) {
     if (!(mask & (1 << k))) return (size_t)-1;
     cudaEvent_t a = take(), b = take();
@@ -98,8 +99,7 @@ struct ProfRun {
   void post(size_t idx, cudaStream_t st) {
     if (idx != (size_t)-1) cudaEventRecord(evs[idx + 1], st);
   }
-  // after the stream has been synchronized
-  void finish() {
+  void finish() {  // after the stream has been synchronized
     if (evs.empty()) return;
     std::lock_guard<std::mutex> lk(g_prof_mutex);
     for (auto& mk : marks) {
@@ -122,24 +122,24 @@ int setup_attributes(int dev) {
   std::lock_guard<std::mutex> lk(g_attr_mutex);
   if (dev < 0 || dev >= 64) return JAC_ECUDA;
   if (g_attr_done[dev]) return 0;
-  if (cudaFuncSetAttribute(k_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGramSmem) != cudaSuccess)
+  bool ok = true;
+  ok &= cudaFuncSetAttribute(k_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGramSmem) == cudaSuccess;
+  ok &= cudaFuncSetAttribute(k_gram, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess;
+  ok &= cudaFuncSetAttribute(k_gram32, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess;
+  ok &= cudaFuncSetAttribute(k_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kUpdSmem) == cudaSuccess;
+  ok &= pivot_set_attributes() == 0;
+  ok &= pivot64_set_attributes() == 0;
+  ok &= cudaFuncSetAttribute(k_rank, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
     return JAC_ECUDA;
-  if (cudaFuncSetAttribute(k_gram, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
-    return JAC_ECUDA;
-  if (cudaFuncSetAttribute(k_gram32, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
-    return JAC_ECUDA;
-  if (cudaFuncSetAttribute(k_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kUpdSmem) != cudaSuccess)
-    return JAC_ECUDA;
-  if (cudaFuncSetAttribute(k_pivot, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pivot_smem_bytes()) !=
-      cudaSuccess)
-    return JAC_ECUDA;
-  if (cudaFuncSetAttribute(k_rank, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024) != cudaSuccess)
-    return JAC_ECUDA;
+  }
   g_attr_done[dev] = true;
   return 0;
 }
 
-// Carves one cudaMallocAsync block into 256-byte aligned pieces.
+// Carves one cudaMallocAsync block into 256-byte aligned pieces (a first pass with base == NULL
+// only measures).
 struct Arena {
   size_t off = 0;
   char* base = nullptr;
@@ -152,81 +152,14 @@ struct Arena {
   }
 };
 
-struct Layout {
-  double *Gw, *Vw, *Ap, *vp, *weights, *nrm2, *lam, *Mn;
-  float *G32, *V32, *Mf, *Vf;
-  int *boff, *perm_in, *pairs, *counts, *skip, *order, *nsteps, *rank;
-  int8_t *Js, *Jin;
-  PairStat* stats;
-  SweepRecord* rec;
-  unsigned* err;
-  unsigned long long* mmax;
-};
-
-size_t carve(Arena& ar, Layout& L, int m, int mp, int np, int n, int nb, int max_steps, bool have_vw, bool weights,
-             bool need_g32, bool mixed) {
-  (void)m;
-  const int half = nb / 2;
-  const int npairs = nb * (nb - 1) / 2;
-  L.Gw = ar.take<double>((size_t)mp * n);
-  L.Vw = have_vw ? ar.take<double>((size_t)np * n) : nullptr;
-  L.Ap = ar.take<double>((size_t)half * JAC_KMAX * JAC_KMAX);
-  L.vp = ar.take<double>((size_t)half * JAC_KMAX * JAC_KMAX);
-  L.weights = weights ? ar.take<double>((size_t)nb * nb) : nullptr;
-  L.nrm2 = ar.take<double>(n);
-  L.lam = ar.take<double>(n);
-  L.Mn = mixed ? ar.take<double>((size_t)n * n) : nullptr;
-  L.G32 = need_g32 ? ar.take<float>((size_t)mp * n) : nullptr;
-  L.V32 = mixed ? ar.take<float>((size_t)np * n) : nullptr;
-  L.Mf = mixed ? ar.take<float>((size_t)n * n) : nullptr;
-  L.Vf = mixed ? ar.take<float>((size_t)n * n) : nullptr;
-  L.boff = ar.take<int>(nb + 1);
-  L.perm_in = ar.take<int>(n);
-  L.pairs = ar.take<int>((size_t)max_steps * half * 2);
-  L.counts = ar.take<int>(max_steps);
-  L.skip = ar.take<int>(half);
-  L.order = weights ? ar.take<int>(npairs) : nullptr;
-  L.nsteps = ar.take<int>(1);
-  L.rank = ar.take<int>(n);
-  L.Js = ar.take<int8_t>(n);
-  L.Jin = ar.take<int8_t>(n);
-  L.stats = ar.take<PairStat>((size_t)max_steps * half);
-  L.rec = ar.take<SweepRecord>(1);
-  L.err = ar.take<unsigned>(1);
-  L.mmax = ar.take<unsigned long long>(1);
-  return ar.off;
-}
-
-int choose_cluster(int half, int mp) {
-  int cs = 1;
-  while (cs * 2 <= 16 && half * cs * 2 <= 2 * 152 && mp / (cs * 2) >= 16) cs *= 2;
-  return cs;
-}
-
-template <class Kern, class... Args>
-int launch_cluster(Kern kern, int half, int CS, int threads, size_t smem, cudaStream_t st, Args... args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(half * CS);
-  cfg.blockDim = dim3(threads);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = CS;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kern, args...) == cudaSuccess ? 0 : JAC_ECUDA;
-}
-
-// Validates the options; returns 0 or the (negative) argument position of opts.
-int check_opts(const jac_opts& o, int argpos) {
+int check_opts(const jac_opts& o, int argpos, bool batch) {
   if (o.block_w < 1 || o.block_w > JAC_WMAX) return -argpos;
   if (o.ordering < 0 || o.ordering > 3) return -argpos;
+  if (batch && o.ordering == JAC_ORDER_CYCLE_WEIGHT) return -argpos;
   if (o.block_mode != JAC_BLOCK_FULL) return -argpos;
   if (o.factor != JAC_FACTOR_CHOL && o.factor != JAC_FACTOR_CHOL_SIGNPIV) return -argpos;
-  if (o.precision != JAC_PREC_FP64 && o.precision != JAC_PREC_FP32) return -argpos;
+  if (o.precision < JAC_PREC_FP64 || o.precision > JAC_PREC_FP32_ONLY) return -argpos;
+  if (batch && o.precision == JAC_PREC_FP32) return -argpos;
   if (o.max_sweeps < 1) return -argpos;
   if (o.want_v != 0 && o.want_v != 1) return -argpos;
   return 0;
@@ -240,10 +173,142 @@ int compute_nb(int n, int w) {
   return nb;
 }
 
+int choose_cluster(int half, int mp) {
+  int cs = 1;
+  while (cs * 2 <= 16 && half * cs * 2 <= 2 * 152 && mp / (cs * 2) >= 16) cs *= 2;
+  return cs;
+}
+
+template <class Kern, class... Args>
+int launch_cluster(Kern kern, dim3 grid, int CS, int threads, size_t smem, cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CS;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, args...) == cudaSuccess ? 0 : JAC_ECUDA;
+}
+
+// Block width of one problem of a batch, by size class: the whole problem is one pivot block up
+// to n = 64 (nb = 2, one step per sweep, KM = 32 while n <= 32), blocks of 32 columns above
+// (nb = 4, three round-robin steps of two pivot blocks).
+int batch_width(int n) { return n <= 64 ? (n + 1) / 2 : 32; }
+
+// Per-problem plan: sizes of its pieces.
+struct Plan {
+  int m, n, mp, np, nb, half, nsteps, km, ordering;
+  bool want_v, have_vw, lowp;
+  std::vector<int> boff;
+};
+
+void make_plan(Plan& P, int m, int n, int w, int ordering, bool want_v, bool have_vw, bool lowp) {
+  P.m = m;
+  P.n = n;
+  P.mp = (m + 15) & ~15;
+  P.np = (n + 15) & ~15;
+  P.nb = compute_nb(n, w);
+  P.half = P.nb / 2;
+  P.ordering = ordering;
+  P.nsteps = (ordering == JAC_ORDER_ROUND_ROBIN) ? P.nb - 1 : (ordering == JAC_ORDER_CYCLE_WEIGHT ? 2 * P.nb : P.nb);
+  P.boff.resize(P.nb + 1);
+  const int base = n / P.nb, rem = n % P.nb;
+  int off = 0, wmax = 0;
+  for (int b = 0; b < P.nb; ++b) {
+    P.boff[b] = off;
+    const int wb = base + (b < rem ? 1 : 0);
+    wmax = std::max(wmax, wb);
+    off += wb;
+  }
+  P.boff[P.nb] = off;
+  P.km = (2 * wmax <= 32) ? 32 : 64;
+  P.want_v = want_v;
+  P.have_vw = have_vw;
+  P.lowp = lowp;
+}
+
+// Device pieces of one problem (pointers into the arena).
+void carve_problem(Arena& ar, const Plan& P, JacProb& d, JacIO& io, bool weights) {
+  d.Gw = ar.take<double>((size_t)P.mp * P.n);
+  d.Vw = P.have_vw ? ar.take<double>((size_t)P.np * P.n) : nullptr;
+  d.G32 = (P.lowp || weights) ? ar.take<float>((size_t)P.mp * P.n) : nullptr;
+  d.V32 = (P.lowp && P.have_vw) ? ar.take<float>((size_t)P.np * P.n) : nullptr;
+  d.mp = P.mp;
+  d.np = P.np;
+  d.n = P.n;
+  d.nb = P.nb;
+  d.half = P.half;
+  d.nsteps = P.nsteps;
+  d.apld = P.km;
+  d.Ap = ar.take<double>((size_t)P.half * P.km * P.km);
+  d.vp = ar.take<double>((size_t)P.half * P.km * P.km);
+  d.active = 1;
+  d.skip = ar.take<int>(P.half);
+  d.stats = ar.take<PairStat>((size_t)P.nsteps * P.half);
+  io.perm_in = ar.take<int>(P.n);
+  io.nrm2 = ar.take<double>(P.n);
+  io.lam = ar.take<double>(P.n);
+  io.rank = ar.take<int>(P.n);
+  io.m = P.m;
+  io.flags = 0;
+  io.sweeps = 0;
+  io.rotations = 0;
+}
+
+// One launch of the three step kernels for every problem of a class array.
+int launch_step(JacProb* dprobs, int count, int km, int max_half, int gslabs, int tslabs, int CS, int s, bool lowp,
+                const PivotParams& pp, cudaStream_t st, ProfRun& prof, long long& launches) {
+  int r = 0;
+  size_t pm = prof.pre(JAC_KERNEL_GRAM, st);
+  if (lowp)
+    r = launch_cluster(k_gram32, dim3(max_half * CS, count), CS, 128, 0, st, (const JacProb*)dprobs, s, CS);
+  else
+    r = launch_cluster(k_gram, dim3(max_half * CS, count), CS, 128, kGramSmem, st, (const JacProb*)dprobs, s, CS);
+  prof.post(pm, st);
+  if (r) return r;
+  pm = prof.pre(JAC_KERNEL_PIVOT, st);
+  pivot_launch(km, max_half, count, st, dprobs, s, pp);
+  pivot64_launch(km, max_half, count, st, dprobs, s, pp);  // blocks the FP32 kernel handed over
+  prof.post(pm, st);
+  pm = prof.pre(JAC_KERNEL_UPDATE, st);
+  if (lowp)
+    k_update32<<<dim3(max_half, tslabs, count), 256, 0, st>>>(dprobs, s, gslabs);
+  else
+    k_update<<<dim3(max_half, tslabs, count), 128, kUpdSmem, st>>>(dprobs, s, gslabs);
+  prof.post(pm, st);
+  launches += 4;
+  return cudaGetLastError() == cudaSuccess ? 0 : JAC_ECUDA;
+}
+
 struct ArgPos {  // 1-based positions of the arguments in the public signature
   int m, n, dtype, G, ldg, J, opts, lambda, U, ldu, V, ldv;
 };
 
+// Extra device pieces of a single solve.
+struct Single {
+  JacProb* probs;
+  JacIO* io;
+  SweepRecord* rec;
+  unsigned* flags;
+  int8_t* Js;
+  long long* jsoff;
+  int* pairs;
+  int* counts;
+  double* weights;
+  int* order;
+  double* Mn;
+  float* Mf;
+  float* Vf;
+  unsigned long long* mmax;
+};
+
+// ------------------------------------------------------------------ single solve
 int solve(int m, int n, int dtype, void* Gv, int ldg, const int8_t* Jdev, const jac_opts* opts_in, double* lambda,
           void* Uv, int ldu, void* Vv, int ldv, jac_info* info, cudaStream_t st, const ArgPos& ap) {
   jac_opts o;
@@ -260,119 +325,121 @@ int solve(int m, int n, int dtype, void* Gv, int ldg, const int8_t* Jdev, const 
   if (!Gv) return fail_arg(ap.G);
   if (ldg < m) return fail_arg(ap.ldg);
   if (ap.J && !Jdev) return fail_arg(ap.J);
-  if (int r = check_opts(o, ap.opts)) return fail_arg(-r);
+  if (int r = check_opts(o, ap.opts, false)) return fail_arg(-r);
   if (!lambda) return fail_arg(ap.lambda);
   if (Uv && ldu < m) return fail_arg(ap.ldu);
   if (Uv && Uv == Gv) return fail_arg(ap.U);
   if (o.want_v && !Vv) return fail_arg(ap.V);
   if (Vv && ldv < n) return fail_arg(ap.ldv);
-  if (o.tol <= 0.0) o.tol = (double)n * 1.1102230246251565e-16;
+  const bool fp32_only = (o.precision == JAC_PREC_FP32_ONLY);
+  if (o.tol <= 0.0)
+    o.tol = fp32_only ? std::max((double)n, 8.0 * std::sqrt((double)m)) * 5.9604644775390625e-08
+                      : (double)n * 1.1102230246251565e-16;
 
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return JAC_ECUDA;
   if (int r = setup_attributes(dev)) return r;
 
-  // signs on the host (needed for the internal sort)
-  std::vector<int8_t> Jh(n, 1);
-  if (ap.J) {
-    if (cudaMemcpyAsync(Jh.data(), Jdev, n, cudaMemcpyDeviceToHost, st) != cudaSuccess) return JAC_ECUDA;
-    if (cudaStreamSynchronize(st) != cudaSuccess) return JAC_ECUDA;
-    for (int k = 0; k < n; ++k)
-      if (Jh[k] != 1 && Jh[k] != -1) return fail_arg(ap.J);
-  }
-  std::vector<int> perm_in;
-  perm_in.reserve(n);
-  for (int k = 0; k < n; ++k)
-    if (Jh[k] > 0) perm_in.push_back(k);
-  for (int k = 0; k < n; ++k)
-    if (Jh[k] < 0) perm_in.push_back(k);
-  std::vector<int8_t> Js(n);
-  for (int k = 0; k < n; ++k) Js[k] = Jh[perm_in[k]];
-
-  const int mp = (m + 15) & ~15, np = (n + 15) & ~15;
-  const int nb = compute_nb(n, o.block_w);
-  const int half = nb / 2;
-  std::vector<int> boff(nb + 1);
-  {
-    const int base = n / nb, rem = n % nb;
-    int off = 0;
-    for (int b = 0; b < nb; ++b) {
-      boff[b] = off;
-      off += base + (b < rem ? 1 : 0);
-    }
-    boff[nb] = off;
-  }
   const bool weights = (o.ordering == JAC_ORDER_CYCLE_WEIGHT);
   const bool mixed = (o.precision == JAC_PREC_FP32);
-  const int max_steps = (o.ordering == JAC_ORDER_ROUND_ROBIN) ? nb - 1 : (weights ? 2 * nb : nb);
+  const bool lowp = mixed || fp32_only;
   const bool want_v = o.want_v != 0;
-  const bool have_vw = want_v || mixed;  // the mixed mode needs V internally for G = G_in V
-  const bool need_g32 = mixed || weights;
+  const bool have_vw = want_v || mixed;  // the mixed mode needs V for G = G_in V
+  Plan P;
+  make_plan(P, m, n, o.block_w, o.ordering, want_v, have_vw, lowp);
 
+  JacProb hp = {};
+  JacIO hio = {};
+  int* boff_dev = nullptr;
+  Single L;
+  auto carve_all = [&](Arena& A) {
+    carve_problem(A, P, hp, hio, weights);
+    boff_dev = A.take<int>(P.nb + 1);
+    L.probs = A.take<JacProb>(1);
+    L.io = A.take<JacIO>(1);
+    L.rec = A.take<SweepRecord>(1);
+    L.flags = A.take<unsigned>(1);
+    L.Js = A.take<int8_t>(n);
+    L.jsoff = A.take<long long>(1);
+    L.pairs = A.take<int>((size_t)P.nsteps * P.half * 2);
+    L.counts = A.take<int>(P.nsteps);
+    L.weights = weights ? A.take<double>((size_t)P.nb * P.nb) : nullptr;
+    L.order = weights ? A.take<int>(P.nb * (P.nb - 1) / 2) : nullptr;
+    L.Mn = mixed ? A.take<double>((size_t)n * n) : nullptr;
+    L.Mf = mixed ? A.take<float>((size_t)n * n) : nullptr;
+    L.Vf = mixed ? A.take<float>((size_t)n * n) : nullptr;
+    L.mmax = A.take<unsigned long long>(1);
+  };
   Arena ar;
-  Layout L;
-  const size_t bytes = carve(ar, L, m, mp, np, n, nb, max_steps, have_vw, weights, need_g32, mixed);
+  carve_all(ar);
   void* base = nullptr;
-  if (cudaMallocAsync(&base, bytes, st) != cudaSuccess) {
+  if (cudaMallocAsync(&base, ar.off, st) != cudaSuccess) {
     cudaGetLastError();
     return JAC_ENOMEM;
   }
   Arena ar2;
   ar2.base = static_cast<char*>(base);
-  carve(ar2, L, m, mp, np, n, nb, max_steps, have_vw, weights, need_g32, mixed);
+  carve_all(ar2);
+  hp.boff = boff_dev;
+  hp.Js = L.Js;
+  hp.pairs = L.pairs;
+  hp.counts = L.counts;
+  hp.pflags = L.flags;
+  hio.G = static_cast<double*>(Gv);
+  hio.ldg = ldg;
+  hio.J = Jdev;
+  hio.lambda = lambda;
+  hio.U = static_cast<double*>(Uv);
+  hio.ldu = ldu;
+  hio.V = want_v ? static_cast<double*>(Vv) : nullptr;
+  hio.ldv = ldv;
 
   int status = JAC_OK;
   auto ck = [&](cudaError_t e) {
     if (e != cudaSuccess && status == JAC_OK) status = JAC_ECUDA;
   };
-  ck(cudaMemcpyAsync(L.boff, boff.data(), sizeof(int) * (nb + 1), cudaMemcpyHostToDevice, st));
-  ck(cudaMemcpyAsync(L.perm_in, perm_in.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
-  ck(cudaMemcpyAsync(L.Js, Js.data(), n, cudaMemcpyHostToDevice, st));
-  ck(cudaMemcpyAsync(L.Jin, Jh.data(), n, cudaMemcpyHostToDevice, st));
-  ck(cudaMemsetAsync(L.err, 0, sizeof(unsigned), st));
+  const long long zero = 0;
+  ck(cudaMemcpyAsync(boff_dev, P.boff.data(), sizeof(int) * (P.nb + 1), cudaMemcpyHostToDevice, st));
+  ck(cudaMemcpyAsync(L.probs, &hp, sizeof(JacProb), cudaMemcpyHostToDevice, st));
+  ck(cudaMemcpyAsync(L.io, &hio, sizeof(JacIO), cudaMemcpyHostToDevice, st));
+  ck(cudaMemcpyAsync(L.jsoff, &zero, sizeof(long long), cudaMemcpyHostToDevice, st));
+  ck(cudaMemsetAsync(L.flags, 0, sizeof(unsigned), st));
 
-  long long launches = have_vw ? 3 : 2;
-  const double* G = static_cast<const double*>(Gv);
-  const int ew_blocks = std::min(1024, (int)(((size_t)mp * n + 255) / 256));
-  k_check_finite<<<std::min(1024, (int)(((size_t)m * n + 255) / 256)), 256, 0, st>>>(G, ldg, m, n, L.err);
-  k_gather_in<<<dim3((mp + 255) / 256, n), 256, 0, st>>>(G, ldg, m, mp, L.perm_in, L.Gw);
-  if (have_vw) k_init_v<<<dim3((np + 255) / 256, n), 256, 0, st>>>(n, np, L.perm_in, L.Vw);
-  ck(cudaGetLastError());
-  unsigned herr = 0;
-  ck(cudaMemcpyAsync(&herr, L.err, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  long long launches = 0;
+  k_sort_signs<<<1, 32, 0, st>>>(L.probs, L.io, L.Js, L.jsoff);
+  k_check_finite<<<dim3(std::min(1024, (int)(((size_t)m * n + 255) / 256)), 1), 256, 0, st>>>(L.probs, L.io);
+  launches += 2;
+  JacIO hio_back;
+  ck(cudaMemcpyAsync(&hio_back, L.io, sizeof(JacIO), cudaMemcpyDeviceToHost, st));
   ck(cudaStreamSynchronize(st));
-  if (status == JAC_OK && (herr & JAC_DEVERR_NONFINITE)) status = JAC_ENONFINITE;
+  if (status == JAC_OK && (hio_back.flags & 2)) {
+    cudaFreeAsync(base, st);
+    cudaStreamSynchronize(st);
+    return fail_arg(ap.J);
+  }
+  if (status == JAC_OK && (hio_back.flags & 1)) status = JAC_ENONFINITE;
+  k_gather_in<<<dim3((P.mp + 255) / 256, n, 1), 256, 0, st>>>(L.probs, L.io);
+  if (have_vw) k_init_v<<<dim3((P.np + 255) / 256, n, 1), 256, 0, st>>>(L.probs, L.io);
+  launches += have_vw ? 2 : 1;
+  ck(cudaGetLastError());
 
-  int nsteps = max_steps;
+  int nsteps = P.nsteps;
   if (status == JAC_OK && !weights) {
-    k_sched_static<<<max_steps, 128, 0, st>>>(nb, o.ordering, max_steps, L.pairs, L.counts);
+    k_sched_static<<<P.nsteps, 128, 0, st>>>(P.nb, o.ordering, P.nsteps, L.pairs, L.counts);
     ++launches;
     ck(cudaGetLastError());
   }
-
-  JacStepArgs args;
-  args.Gw = L.Gw;
-  args.mp = mp;
-  args.Vw = L.Vw;
-  args.np = np;
-  args.n = n;
-  args.nb = nb;
-  args.boff = L.boff;
-  args.Js = L.Js;
-  args.pairs = L.pairs;
-  args.counts = L.counts;
-  args.half = half;
-  const int CS = choose_cluster(half, mp);
-  const int gslabs = (mp + 63) / 64;
-  const int vslabs = have_vw ? (np + 63) / 64 : 0;
-  // FP32 phase: stop at the scaled off-norm the FP32 Gram still resolves (its entries carry
-  // errors ~ eps_32 sqrt(m) relative to ||g_i|| ||g_j||)
+  const int CS = choose_cluster(P.half, P.mp);
+  const int gslabs = (P.mp + 63) / 64;
+  const int tslabs = gslabs + (have_vw ? (P.np + 63) / 64 : 0);
+  const int ew_blocks = std::min(1024, (int)(((size_t)P.mp * n + 255) / 256));
+  // FP32 sweeps of the mixed mode stop at the scaled off-norm the FP32 Gram still resolves (its
+  // entries carry errors ~ eps_32 sqrt(m) relative to ||g_i|| ||g_j||)
   const double tau_lo = std::max(o.tol, 8.0 * 5.9604644775390625e-08 * std::sqrt((double)m));
-  int phase = mixed ? 1 : 3;
-  if (mixed && status == JAC_OK) {
-    k_cvt64to32<<<ew_blocks, 256, 0, st>>>(mp, n, L.Gw, mp, L.G32, mp, nullptr);
-    k_cvt64to32<<<ew_blocks, 256, 0, st>>>(np, n, L.Vw, np, L.V32, np, nullptr);
-    launches += 2;
+  int phase = mixed ? 1 : (fp32_only ? 4 : 3);  // 1: FP32 sweeps of the mixed mode, 3: FP64, 4: FP32 only
+  if (lowp && status == JAC_OK) {
+    k_lowp_copy<<<dim3(ew_blocks, 1), 256, 0, st>>>(L.probs, 0);  // FP64 layout -> FP32 copies
+    launches += 1;
     ck(cudaGetLastError());
   }
 
@@ -384,56 +451,37 @@ int solve(int m, int n, int dtype, void* Gv, int ldg, const int8_t* Jdev, const 
   ProfRun prof;
   prof.begin();
   for (int sw = 0; status == JAC_OK && n > 1 && sw < o.max_sweeps; ++sw) {
-    const bool low = (phase == 1);
+    const bool low = (phase == 1 || phase == 4);
     PivotParams pp;
-    pp.tol = low ? tau_lo : o.tol;
+    pp.tol = (phase == 1) ? tau_lo : o.tol;
+    pp.tol_eps = 0.0;
+    pp.tol_m = 0.0;
     pp.factor = o.factor;
     pp.ns_mode = low ? 0 : 1;
     if (weights) {
-      const int npairs = nb * (nb - 1) / 2;
+      const int npairs = P.nb * (P.nb - 1) / 2;
       if (!low) {
-        k_cvt64to32<<<ew_blocks, 256, 0, st>>>(mp, n, L.Gw, mp, L.G32, mp, nullptr);
+        k_cvt64to32<<<ew_blocks, 256, 0, st>>>(P.mp, n, hp.Gw, P.mp, hp.G32, P.mp, nullptr);
         ++launches;
       }
-      k_block_weights32<<<npairs, 256, 0, st>>>(L.G32, mp, nb, L.boff, L.weights);
-      k_sched_cycle_weight<<<1, 1024, sizeof(int) * nb, st>>>(nb, L.weights, L.order, L.pairs, L.counts,
-                                                              max_steps, L.nsteps);
+      int* nsteps_dev = reinterpret_cast<int*>(reinterpret_cast<char*>(L.probs) + offsetof(JacProb, nsteps));
+      k_block_weights32<<<npairs, 256, 0, st>>>(hp.G32, P.mp, P.nb, boff_dev, L.weights);
+      k_sched_cycle_weight<<<1, 1024, sizeof(int) * P.nb, st>>>(P.nb, L.weights, L.order, L.pairs, L.counts,
+                                                                P.nsteps, nsteps_dev);
       launches += 2;
       ck(cudaGetLastError());
-      ck(cudaMemcpyAsync(&nsteps, L.nsteps, sizeof(int), cudaMemcpyDeviceToHost, st));
+      ck(cudaMemcpyAsync(&nsteps, nsteps_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
       ck(cudaStreamSynchronize(st));
       if (status != JAC_OK) break;
-      if (nsteps < 1 || nsteps > max_steps) {
+      if (nsteps < 1 || nsteps > P.nsteps) {
         status = JAC_EINTERNAL;
         break;
       }
     }
-    for (int s = 0; s < nsteps && status == JAC_OK; ++s) {
-      const int* sp = L.pairs + (size_t)s * half * 2;
-      const int* sc = L.counts + s;
-      size_t pm = prof.pre(JAC_KERNEL_GRAM, st);
-      if (low) {
-        if (int r = launch_cluster(k_gram32, half, CS, 128, 0, st, args, (const float*)L.G32, sp, sc, CS, L.Ap))
-          status = r;
-      } else {
-        if (int r = launch_cluster(k_gram, half, CS, 128, kGramSmem, st, args, sp, sc, CS, L.Ap)) status = r;
-      }
-      prof.post(pm, st);
-      pm = prof.pre(JAC_KERNEL_PIVOT, st);
-      k_pivot<<<half, 1024, pivot_smem_bytes(), st>>>(args, sp, sc, L.Ap, pp, L.vp, L.skip,
-                                                      L.stats + (size_t)s * half, L.err);
-      prof.post(pm, st);
-      pm = prof.pre(JAC_KERNEL_UPDATE, st);
-      if (low) {
-        k_update32<<<dim3(half, gslabs + vslabs), 256, 0, st>>>(args, L.G32, L.V32, sp, sc, L.vp, L.skip, gslabs);
-      } else {
-        k_update<<<dim3(half, gslabs + vslabs), 128, kUpdSmem, st>>>(args, sp, sc, L.vp, L.skip, gslabs);
-      }
-      prof.post(pm, st);
-      launches += 3;
-      ck(cudaGetLastError());
-    }
-    k_sweep_reduce<<<1, 256, 0, st>>>(L.stats, L.counts, nsteps, half, nb, L.err, L.rec);
+    for (int s = 0; s < nsteps && status == JAC_OK; ++s)
+      if (int r = launch_step(L.probs, 1, P.km, P.half, gslabs, tslabs, CS, s, low, pp, st, prof, launches))
+        status = r;
+    k_sweep_reduce<<<1, 256, 0, st>>>(L.probs, L.io, L.rec, 0, nullptr);
     ++launches;
     ck(cudaGetLastError());
     ck(cudaMemcpyAsync(&hrec, L.rec, sizeof(SweepRecord), cudaMemcpyDeviceToHost, st));
@@ -447,24 +495,33 @@ int solve(int m, int n, int dtype, void* Gv, int ldg, const int8_t* Jdev, const 
     ns_total += hrec.ns_steps;
     inner_total += hrec.inner_sweeps;
     for (int u = 0; u < 4; ++u) cyc_total[u] += hrec.cyc[u];
+    bool lowp_singular = false;
     if (hrec.err & JAC_DEVERR_NOTPD) {
-      status = JAC_ENOTPD;
-      break;
+      if (phase != 1) {
+        status = JAC_ENOTPD;
+        break;
+      }
+      // a block whose FP32 Gram is singular at FP32 precision: the FP64 phase decides
+      lowp_singular = true;
+      static const int kActive = 1;
+      ck(cudaMemsetAsync(L.flags, 0, sizeof(unsigned), st));
+      ck(cudaMemcpyAsync(reinterpret_cast<char*>(L.probs) + offsetof(JacProb, active), &kActive, sizeof(int),
+                         cudaMemcpyHostToDevice, st));
     }
-    if (low) {
+    if (phase == 1) {
       ++lowp_sweeps;
-      // leave the FP32 phase when it has converged at tau_lo, when the off-norm stalls, or
-      // when only the sweeps the polish needs are left
+      // leave the FP32 phase when it has converged at tau_lo, when the off-norm stalls, when a
+      // block is singular in FP32, or when only the sweeps the polish needs are left
       const bool stalled = hrec.max_scaled < 1e-3 && hrec.max_scaled > 0.5 * prev_max;
-      const bool done = hrec.pivots_rotated == 0 || stalled || sw + 4 >= o.max_sweeps;
+      const bool done = hrec.pivots_rotated == 0 || stalled || lowp_singular || sw + 4 >= o.max_sweeps;
       prev_max = hrec.max_scaled;
       if (done) {
-        // phase 2: V (FP32) -> FP64, J-unitary by Newton-Schulz, then G = G_in V
-        k_cvt32to64<<<ew_blocks, 256, 0, st>>>(np, n, L.V32, np, L.Vw, np);
+        // V (FP32) -> FP64, J-unitary by Newton-Schulz, then G = G_in V
+        k_cvt32to64<<<ew_blocks, 256, 0, st>>>(P.np, n, hp.V32, P.np, hp.Vw, P.np);
         launches += 1;
-        const dim3 gsym((n + 31) / 32, (n + 31) / 32);
+        const dim3 gsym((n + 31) / 32, (n + 31) / 32, 1);
         for (int it = 0; it < 4 && status == JAC_OK; ++it) {
-          k_gemm64<<<gsym, 128, 0, st>>>(n, n, n, L.Vw, np, 1, L.Vw, np, L.Jin, L.Js, L.Mn, n, 1);
+          k_gemm64<<<gsym, 128, 0, st>>>(n, n, n, hp.Vw, P.np, 1, hp.Vw, P.np, Jdev, L.Js, L.Mn, n, 1, 0, 0, 0, 0);
           ck(cudaMemsetAsync(L.mmax, 0, sizeof(unsigned long long), st));
           k_absmax64<<<std::min(1024, (n * n + 255) / 256), 256, 0, st>>>(n, L.Mn, n, L.mmax);
           unsigned long long hm = 0;
@@ -480,16 +537,16 @@ int solve(int m, int n, int dtype, void* Gv, int ldg, const int8_t* Jdev, const 
           if (mm <= 4e-16) break;
           // V <- V - V (J_c M) / 2, the correction in FP32
           k_cvt64to32<<<ew_blocks, 256, 0, st>>>(n, n, L.Mn, n, L.Mf, n, L.Js);
-          k_cvt64to32<<<ew_blocks, 256, 0, st>>>(n, n, L.Vw, np, L.Vf, n, nullptr);
-          k_ns_correct<<<dim3((n + 63) / 64, (n + 63) / 64), 256, 0, st>>>(n, n, n, L.Vf, n, L.Mf, n, L.Vw, np);
+          k_cvt64to32<<<ew_blocks, 256, 0, st>>>(n, n, hp.Vw, P.np, L.Vf, n, nullptr);
+          k_ns_correct<<<dim3((n + 63) / 64, (n + 63) / 64), 256, 0, st>>>(n, n, n, L.Vf, n, L.Mf, n, hp.Vw, P.np);
           launches += 3;
           ++ns_global;
           ck(cudaGetLastError());
           if (mm * mm + 1e-6 * mm <= 2e-16) break;
         }
         // G_int = G_in V (V rows are input columns): the FP64 factor the polish works on
-        k_gemm64<<<dim3((m + 31) / 32, (n + 31) / 32), 128, 0, st>>>(m, n, n, G, ldg, 0, L.Vw, np, nullptr,
-                                                                     nullptr, L.Gw, mp, 0);
+        k_gemm64<<<dim3((m + 31) / 32, (n + 31) / 32, 1), 128, 0, st>>>(m, n, n, hio.G, ldg, 0, hp.Vw, P.np, nullptr,
+                                                                        nullptr, hp.Gw, P.mp, 0, 0, 0, 0, 0);
         ++launches;
         ck(cudaGetLastError());
         phase = 3;
@@ -503,13 +560,14 @@ int solve(int m, int n, int dtype, void* Gv, int ldg, const int8_t* Jdev, const 
   }
   if (n == 1) converged = 1;
   if (status == JAC_OK && !converged) status = JAC_ENOTCONV;
-
+  if (phase == 4 && (status == JAC_OK || status == JAC_ENOTCONV)) {
+    k_lowp_copy<<<dim3(ew_blocks, 1), 256, 0, st>>>(L.probs, 1);  // FP32 result -> FP64 layout
+    ++launches;
+  }
   if (status == JAC_OK || status == JAC_ENOTCONV) {
-    k_colnorm<<<(n * 32 + 255) / 256, 256, 0, st>>>(L.Gw, mp, n, L.Js, L.nrm2, L.lam);
-    k_rank<<<(n + 255) / 256, 256, sizeof(unsigned long long) * n, st>>>(L.lam, n, L.rank);
-    k_scatter<<<n, 128, 0, st>>>(L.Gw, mp, m, L.Vw, np, n, L.nrm2, L.lam, L.rank, lambda, static_cast<double*>(Gv),
-                                 ldg, static_cast<double*>(Uv), ldu, want_v ? static_cast<double*>(Vv) : nullptr,
-                                 ldv);
+    k_colnorm<<<dim3((n * 32 + 255) / 256, 1), 256, 0, st>>>(L.probs, L.io);
+    k_rank<<<dim3((n + 255) / 256, 1), 256, sizeof(unsigned long long) * n, st>>>(L.probs, L.io);
+    k_scatter<<<dim3(n, 1), 128, 0, st>>>(L.probs, L.io);
     launches += 3;
     if (cudaGetLastError() != cudaSuccess && status == JAC_OK) status = JAC_ECUDA;
   }
@@ -530,10 +588,263 @@ int solve(int m, int n, int dtype, void* Gv, int ldg, const int8_t* Jdev, const 
     info->lowp_sweeps = lowp_sweeps;
     info->global_ns_steps = ns_global;
     info->pivot_ns_steps = ns_total;
-    info->inner_sweeps = inner_total;
     for (int u = 0; u < 4; ++u) info->pivot_cycles[u] = cyc_total[u];
+    info->inner_sweeps = inner_total;
   }
   return status;
+}
+
+// ------------------------------------------------------------------ batched solve
+// Problems are grouped by pivot class (KM = 32 or 64), largest order first inside a class; all
+// problems advance sweep by sweep in the same launches, and converged ones drop out (active = 0)
+// in the sweep reduction.
+constexpr int kBatchChunk = 32768;  // grid y / z extents stay below 65536
+
+int solve_batched(int batch, const int* m, const int* n, int dtype, void* const* G, const int* ldg,
+                  const int8_t* const* J, const jac_opts* opts_in, double* const* lambda, void* const* U,
+                  const int* ldu, void* const* V, const int* ldv, jac_info* info, cudaStream_t st) {
+  if (batch > kBatchChunk) {  // consecutive chunks; the first failing status in input order wins
+    int first = JAC_OK;
+    for (int b0 = 0; b0 < batch; b0 += kBatchChunk) {
+      const int c = std::min(kBatchChunk, batch - b0);
+      auto off = [&](auto* p) { return p ? p + b0 : p; };
+      const int r = solve_batched(c, off(m), off(n), dtype, off(G), off(ldg), off(J), opts_in, off(lambda), off(U),
+                                  off(ldu), off(V), off(ldv), off(info), st);
+      if (r < 0) return r;  // argument errors are found in the first chunk that has them
+      if (r == JAC_ECUDA || r == JAC_ENOMEM) return r;
+      if (first == JAC_OK) first = r;
+    }
+    return first;
+  }
+  jac_opts o;
+  jacobi_default_opts(&o);
+  if (opts_in) o = *opts_in;
+  if (batch < 0) return -1;
+  if (batch == 0) return JAC_OK;
+  if (!m) return -2;
+  if (!n) return -3;
+  if (dtype != JAC_R64) return -4;
+  if (!G || !ldg) return !G ? -5 : -6;
+  if (int r = check_opts(o, 8, true)) return r;
+  if (!lambda) return -9;
+  if (U && !ldu) return -11;
+  if (o.want_v && (!V || !ldv)) return !V ? -12 : -13;
+  for (int b = 0; b < batch; ++b) {
+    if (m[b] < 1) return -2;
+    if (n[b] < 1 || n[b] > m[b] || n[b] > 128) return -3;
+    if (!G[b]) return -5;
+    if (ldg[b] < m[b]) return -6;
+    if (!lambda[b]) return -9;
+    if (U && U[b] && ldu[b] < m[b]) return -11;
+    if (U && U[b] == G[b]) return -10;
+    if (o.want_v && !V[b]) return -12;
+    if (o.want_v && ldv[b] < n[b]) return -13;
+  }
+  if (info) std::memset(info, 0, sizeof(jac_info) * (size_t)batch);
+  const bool fp32_only = (o.precision == JAC_PREC_FP32_ONLY);
+  const bool want_v = o.want_v != 0;
+  const bool have_vw = want_v;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return JAC_ECUDA;
+  if (int r = setup_attributes(dev)) return r;
+
+  std::vector<Plan> plans(batch);
+  for (int b = 0; b < batch; ++b) make_plan(plans[b], m[b], n[b], batch_width(n[b]), o.ordering, want_v, have_vw,
+                                            fp32_only);
+  // class order: KM 32 then 64; largest n first inside a class
+  std::vector<int> order(batch);
+  for (int b = 0; b < batch; ++b) order[b] = b;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    if (plans[x].km != plans[y].km) return plans[x].km < plans[y].km;
+    return plans[x].n > plans[y].n;
+  });
+  const int count32 = (int)std::count_if(plans.begin(), plans.end(), [](const Plan& p) { return p.km == 32; });
+  const int count64 = batch - count32;
+  std::map<int, std::pair<int*, int*>> tables;  // nb -> (pairs, counts)
+  for (auto& p : plans) tables[p.nb] = {nullptr, nullptr};
+
+  std::vector<JacProb> hp(batch);
+  std::vector<JacIO> hio(batch);
+  std::vector<long long> jsoff(batch);
+  std::vector<int> boff_host;  // block offsets of every problem, concatenated
+  std::vector<size_t> boff_at(batch);
+  long long nsum = 0;
+  for (int i = 0; i < batch; ++i) {
+    jsoff[i] = nsum;
+    nsum += plans[order[i]].n;
+    boff_at[i] = boff_host.size();
+    boff_host.insert(boff_host.end(), plans[order[i]].boff.begin(), plans[order[i]].boff.end());
+  }
+  int* d_boff = nullptr;
+  JacProb* d_probs = nullptr;
+  JacIO* d_io = nullptr;
+  SweepRecord* d_rec = nullptr;
+  unsigned* d_flags = nullptr;
+  int8_t* d_Js = nullptr;
+  long long* d_jsoff = nullptr;
+  int* d_remaining = nullptr;
+  auto carve_all = [&](Arena& A) {
+    for (int i = 0; i < batch; ++i) carve_problem(A, plans[order[i]], hp[i], hio[i], false);
+    d_boff = A.take<int>(boff_host.size());
+    for (auto& kv : tables) {
+      const int nb = kv.first;
+      const int steps = (o.ordering == JAC_ORDER_ROUND_ROBIN) ? nb - 1 : nb;
+      kv.second.first = A.take<int>((size_t)steps * (nb / 2) * 2);
+      kv.second.second = A.take<int>(steps);
+    }
+    d_probs = A.take<JacProb>(batch);
+    d_io = A.take<JacIO>(batch);
+    d_rec = A.take<SweepRecord>(batch);
+    d_flags = A.take<unsigned>(batch);
+    d_Js = A.take<int8_t>(nsum);
+    d_jsoff = A.take<long long>(batch);
+    d_remaining = A.take<int>(1);
+  };
+  Arena ar;
+  carve_all(ar);
+  void* base = nullptr;
+  if (cudaMallocAsync(&base, ar.off, st) != cudaSuccess) {
+    cudaGetLastError();
+    return JAC_ENOMEM;
+  }
+  Arena ar2;
+  ar2.base = static_cast<char*>(base);
+  carve_all(ar2);
+  std::vector<int> boff_all;
+  std::vector<std::pair<int*, size_t>> boff_pieces;
+  for (int i = 0; i < batch; ++i) {
+    const int b = order[i];
+    const Plan& P = plans[b];
+    hp[i].boff = d_boff + boff_at[i];
+    hp[i].Js = d_Js + jsoff[i];
+    hp[i].pairs = tables[P.nb].first;
+    hp[i].counts = tables[P.nb].second;
+    hp[i].pflags = d_flags + i;
+    hio[i].G = static_cast<double*>(G[b]);
+    hio[i].ldg = ldg[b];
+    hio[i].J = J ? J[b] : nullptr;
+    hio[i].lambda = lambda[b];
+    hio[i].U = U ? static_cast<double*>(U[b]) : nullptr;
+    hio[i].ldu = U ? ldu[b] : 0;
+    hio[i].V = want_v ? static_cast<double*>(V[b]) : nullptr;
+    hio[i].ldv = want_v ? ldv[b] : 0;
+  }
+  int status = JAC_OK;
+  auto ck = [&](cudaError_t e) {
+    if (e != cudaSuccess && status == JAC_OK) status = JAC_ECUDA;
+  };
+  ck(cudaMemcpyAsync(d_boff, boff_host.data(), sizeof(int) * boff_host.size(), cudaMemcpyHostToDevice, st));
+  ck(cudaMemcpyAsync(d_probs, hp.data(), sizeof(JacProb) * batch, cudaMemcpyHostToDevice, st));
+  ck(cudaMemcpyAsync(d_io, hio.data(), sizeof(JacIO) * batch, cudaMemcpyHostToDevice, st));
+  ck(cudaMemcpyAsync(d_jsoff, jsoff.data(), sizeof(long long) * batch, cudaMemcpyHostToDevice, st));
+  ck(cudaMemsetAsync(d_flags, 0, sizeof(unsigned) * batch, st));
+  for (auto& kv : tables) {
+    const int nb = kv.first;
+    const int steps = (o.ordering == JAC_ORDER_ROUND_ROBIN) ? nb - 1 : nb;
+    k_sched_static<<<steps, 128, 0, st>>>(nb, o.ordering, steps, kv.second.first, kv.second.second);
+  }
+  int max_mp = 0, max_np = 0, max_n = 0;
+  for (auto& p : plans) {
+    max_mp = std::max(max_mp, p.mp);
+    max_np = std::max(max_np, p.np);
+    max_n = std::max(max_n, p.n);
+  }
+  k_sort_signs<<<batch, 32, 0, st>>>(d_probs, d_io, d_Js, d_jsoff);
+  k_check_finite<<<dim3(8, batch), 256, 0, st>>>(d_probs, d_io);
+  k_apply_flags<<<(batch + 255) / 256, 256, 0, st>>>(d_probs, d_io, batch);
+  k_gather_in<<<dim3((max_mp + 255) / 256, max_n, batch), 256, 0, st>>>(d_probs, d_io);
+  if (have_vw) k_init_v<<<dim3((max_np + 255) / 256, max_n, batch), 256, 0, st>>>(d_probs, d_io);
+  if (fp32_only) k_lowp_copy<<<dim3(8, batch), 256, 0, st>>>(d_probs, 0);
+  ck(cudaGetLastError());
+
+  struct Cls {
+    JacProb* probs;
+    JacIO* io;
+    SweepRecord* rec;
+    int count, km, max_half, max_steps, gslabs, tslabs;
+  };
+  std::vector<Cls> cls;
+  auto add_cls = [&](int first, int count, int km) {
+    if (count <= 0) return;
+    Cls c{d_probs + first, d_io + first, d_rec + first, count, km, 0, 0, 0, 0};
+    for (int i = first; i < first + count; ++i) {
+      const Plan& P = plans[order[i]];
+      c.max_half = std::max(c.max_half, P.half);
+      c.max_steps = std::max(c.max_steps, P.nsteps);
+      c.gslabs = std::max(c.gslabs, (P.mp + 63) / 64);
+      c.tslabs = std::max(c.tslabs, (P.mp + 63) / 64 + (have_vw ? (P.np + 63) / 64 : 0));
+    }
+    cls.push_back(c);
+  };
+  add_cls(0, count32, 32);
+  add_cls(count32, count64, 64);
+  PivotParams pp;
+  pp.tol = o.tol;  // <= 0: n eps of each problem
+  pp.tol_eps = fp32_only ? 5.9604644775390625e-08 : 1.1102230246251565e-16;
+  pp.tol_m = fp32_only ? 8.0 : 0.0;
+  pp.factor = o.factor;
+  pp.ns_mode = fp32_only ? 0 : 1;
+  ProfRun prof;
+  prof.begin();
+  long long launches = 0;
+  int sweeps = 0;
+  for (int sw = 0; status == JAC_OK && sw < o.max_sweeps; ++sw) {
+    ck(cudaMemsetAsync(d_remaining, 0, sizeof(int), st));
+    for (auto& c : cls) {
+      for (int s = 0; s < c.max_steps && status == JAC_OK; ++s)
+        if (int r = launch_step(c.probs, c.count, c.km, c.max_half, c.gslabs, c.tslabs, 1, s, fp32_only, pp, st, prof,
+                                launches))
+          status = r;
+      k_sweep_reduce<<<c.count, 256, 0, st>>>(c.probs, c.io, c.rec, 1, d_remaining);
+      ++launches;
+    }
+    int remaining = 0;
+    ck(cudaMemcpyAsync(&remaining, d_remaining, sizeof(int), cudaMemcpyDeviceToHost, st));
+    ck(cudaStreamSynchronize(st));
+    ++sweeps;
+    if (remaining == 0) break;
+  }
+  if (fp32_only) k_lowp_copy<<<dim3(8, batch), 256, 0, st>>>(d_probs, 1);
+  for (auto& c : cls) {
+    int nmax = 0;
+    for (int i = (int)(c.probs - d_probs); i < (int)(c.probs - d_probs) + c.count; ++i)
+      nmax = std::max(nmax, plans[order[i]].n);
+    k_colnorm<<<dim3((nmax * 32 + 255) / 256, c.count), 256, 0, st>>>(c.probs, c.io);
+    k_rank<<<dim3((nmax + 255) / 256, c.count), 256, sizeof(unsigned long long) * nmax, st>>>(c.probs, c.io);
+    k_scatter<<<dim3(nmax, c.count), 128, 0, st>>>(c.probs, c.io);
+    launches += 3;
+  }
+  ck(cudaGetLastError());
+  std::vector<JacProb> hp_back(batch);
+  std::vector<JacIO> hio_back(batch);
+  std::vector<unsigned> flags_back(batch);
+  ck(cudaMemcpyAsync(hp_back.data(), d_probs, sizeof(JacProb) * batch, cudaMemcpyDeviceToHost, st));
+  ck(cudaMemcpyAsync(hio_back.data(), d_io, sizeof(JacIO) * batch, cudaMemcpyDeviceToHost, st));
+  ck(cudaMemcpyAsync(flags_back.data(), d_flags, sizeof(unsigned) * batch, cudaMemcpyDeviceToHost, st));
+  cudaFreeAsync(base, st);
+  ck(cudaStreamSynchronize(st));
+  prof.finish();
+  int first_bad = JAC_OK;
+  for (int i = 0; i < batch; ++i) {
+    const int b = order[i];
+    int s = JAC_OK;
+    if (hio_back[i].flags & 2) s = -7;
+    else if (hio_back[i].flags & 1) s = JAC_ENONFINITE;
+    else if (flags_back[i] & JAC_DEVERR_NOTPD) s = JAC_ENOTPD;
+    else if (hp_back[i].active) s = JAC_ENOTCONV;
+    if (status != JAC_OK) s = status;
+    if (info) {
+      info[b].status = s;
+      info[b].converged = (s == JAC_OK) ? 1 : 0;
+      info[b].sweeps = hio_back[i].sweeps;
+      info[b].rotations = hio_back[i].rotations;
+      info[b].steps_per_sweep = plans[b].nsteps;
+      info[b].launches = (b == 0) ? launches : 0;
+    }
+    if (s != JAC_OK && first_bad == JAC_OK) first_bad = s;
+  }
+  (void)sweeps;
+  return status != JAC_OK ? status : first_bad;
 }
 
 }  // namespace
@@ -566,7 +877,7 @@ const char* jacobi_status_string(int s) {
   }
 }
 
-int jacobi_version(void) { return 100; }
+int jacobi_version(void) { return 200; }
 
 int jacobi_profile_begin(int mask) {
   if (mask < 0 || mask >= (1 << JAC_KERNEL_COUNT)) return -1;
@@ -607,6 +918,12 @@ int jacobi_eig_pd(int m, int n, int dtype, void* G, int ldg, const jac_opts* opt
                   int ldu, void* V, int ldv, jac_info* info, jac_stream_t stream) {
   const ArgPos ap = {1, 2, 3, 4, 5, 0, 6, 7, 8, 9, 10, 11};
   return solve(m, n, dtype, G, ldg, nullptr, opts, lambda, U, ldu, V, ldv, info, (cudaStream_t)stream, ap);
+}
+
+int jacobi_eig_batched(int batch, const int* m, const int* n, int dtype, void* const* G, const int* ldg,
+                       const int8_t* const* J, const jac_opts* opts, double* const* lambda, void* const* U,
+                       const int* ldu, void* const* V, const int* ldv, jac_info* info, jac_stream_t stream) {
+  return solve_batched(batch, m, n, dtype, G, ldg, J, opts, lambda, U, ldu, V, ldv, info, (cudaStream_t)stream);
 }
 
 int jacobi_sched_pairs(int nb, int ordering, const double* weights, int* pairs, int* counts, int max_steps,

@@ -19,23 +19,23 @@ namespace jac {
 __device__ __forceinline__ int pcol(int c, int wp, int op, int oq) { return c < wp ? op + c : oq + (c - wp); }
 
 // ----------------------------------------------------------------------------- FP32 gram
-// Grid half * CS, cluster (CS,1,1), 128 threads.  Thread (ty = tid / 8, tx = tid % 8) owns
+// Grid (half * CS, nprob), cluster (CS,1,1), 128 threads.  Thread (ty = tid / 8, tx = tid % 8) owns
 // rows 4ty..4ty+3 and columns 8tx..8tx+7 of the 64 x 64 partial.  Partials are added through
 // distributed shared memory and written to Ap (FP64 storage, FP32 accuracy).
 #define G32_RS 32
-__global__ void __launch_bounds__(128) k_gram32(JacStepArgs a, const float* __restrict__ G32,
-                                               const int* __restrict__ step_pairs,
-                                               const int* __restrict__ step_count, int CS,
-                                               double* __restrict__ Ap) {
+__global__ void __launch_bounds__(128) k_gram32(const JacProb* __restrict__ probs, int s, int CS) {
   __shared__ __align__(16) float Xs[G32_RS][JAC_KMAX];
   __shared__ float Cs[JAC_KMAX][JAC_KMAX + 1];
   cg::cluster_group cluster = cg::this_cluster();
+  const JacProb& a = probs[blockIdx.y];
   const int pair = blockIdx.x / CS;
   const int crank = (int)cluster.block_rank();
-  if (pair >= *step_count) return;
-  const int p = step_pairs[2 * pair], q = step_pairs[2 * pair + 1];
+  if (!a.active || s >= a.nsteps || pair >= a.counts[s]) return;  // uniform over the cluster
+  const int* sp = a.pairs + (size_t)s * a.half * 2;
+  const int p = sp[2 * pair], q = sp[2 * pair + 1];
   const int op = a.boff[p], wp = a.boff[p + 1] - op, oq = a.boff[q], wq = a.boff[q + 1] - oq;
   const int k = wp + wq;
+  const float* G32 = a.G32;
   const int tid = threadIdx.x, ty = tid >> 3, tx = tid & 7;
   const int rpc = ((a.mp / CS + 15) & ~15);
   const int r_begin = min(a.mp, crank * rpc), r_end = min(a.mp, r_begin + rpc);
@@ -71,53 +71,53 @@ __global__ void __launch_bounds__(128) k_gram32(JacStepArgs a, const float* __re
   cluster.sync();
   const int tot = k * k, per = (tot + CS - 1) / CS;
   const int e0 = crank * per, e1 = min(tot, e0 + per);
-  double* out = Ap + (size_t)pair * JAC_KMAX * JAC_KMAX;
+  double* out = a.Ap + (size_t)pair * a.apld * a.apld;
   for (int e = e0 + tid; e < e1; e += 128) {
     const int i = e % k, j = e / k;
-    float s = 0.0f;
+    float sum = 0.0f;
     for (int rk = 0; rk < CS; ++rk) {
       const float* rc = cluster.map_shared_rank(&Cs[0][0], rk);
-      s += rc[i * (JAC_KMAX + 1) + j];
+      sum += rc[i * (JAC_KMAX + 1) + j];
     }
-    out[j * JAC_KMAX + i] = (double)s;
+    out[j * a.apld + i] = (double)sum;
   }
   cluster.sync();
 }
 
 // ----------------------------------------------------------------------------- FP32 update
-// Grid (half, nslab), 256 threads; slab = 64 rows of G32 (y < gslabs) or V32.  Y = X V_P in
-// FP32 with V_P read from the FP64 pivot output.  Thread (ty = tid / 16, tx = tid % 16) owns
+// Grid (half, nslab, nprob), 256 threads; slab = 64 rows of G32 (y < gslabs) or V32.  Y = X V_P
+// in FP32 with V_P read from the FP64 pivot output.  Thread (ty = tid / 16, tx = tid % 16) owns
 // rows 4ty..+3 and columns 4tx..+3.
-__global__ void __launch_bounds__(256) k_update32(JacStepArgs a, float* __restrict__ G32, float* __restrict__ V32,
-                                                 const int* __restrict__ step_pairs,
-                                                 const int* __restrict__ step_count, const double* __restrict__ vp,
-                                                 const int* __restrict__ skip, int gslabs) {
+__global__ void __launch_bounds__(256) k_update32(const JacProb* __restrict__ probs, int s, int gslabs) {
   __shared__ __align__(16) float Bs[JAC_KMAX][JAC_KMAX + 4];  // V_P[c][j] row-major in c
   __shared__ __align__(16) float Xs[64][JAC_KMAX + 4];        // X[r][c]
+  const JacProb& a = probs[blockIdx.z];
   const int pair = blockIdx.x;
-  if (pair >= *step_count || skip[pair]) return;
-  const int p = step_pairs[2 * pair], q = step_pairs[2 * pair + 1];
+  if (!a.active || s >= a.nsteps || pair >= a.counts[s] || a.skip[pair]) return;
+  const int* sp = a.pairs + (size_t)s * a.half * 2;
+  const int p = sp[2 * pair], q = sp[2 * pair + 1];
   const int op = a.boff[p], wp = a.boff[p + 1] - op, oq = a.boff[q], wq = a.boff[q + 1] - oq;
   const int k = wp + wq;
   float* base;
   int ld, r0, rs;
   if ((int)blockIdx.y < gslabs) {
-    base = G32;
+    base = a.G32;
     ld = a.mp;
     r0 = blockIdx.y * 64;
     rs = min(64, a.mp - r0);
   } else {
-    base = V32;
+    if (!a.V32) return;
+    base = a.V32;
     ld = a.np;
     r0 = (blockIdx.y - gslabs) * 64;
     rs = min(64, a.np - r0);
   }
   if (rs <= 0) return;
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
-  const double* V = vp + (size_t)pair * JAC_KMAX * JAC_KMAX;
+  const double* V = a.vp + (size_t)pair * a.apld * a.apld;
   for (int idx = tid; idx < JAC_KMAX * JAC_KMAX; idx += 256) {
     const int c = idx % JAC_KMAX, j = idx / JAC_KMAX;
-    Bs[c][j] = (c < k && j < k) ? (float)V[j * JAC_KMAX + c] : 0.0f;
+    Bs[c][j] = (c < k && j < k) ? (float)V[j * a.apld + c] : 0.0f;
   }
   for (int idx = tid; idx < JAC_KMAX * 64; idx += 256) {
     const int r = idx % 64, c = idx / 64;
@@ -152,7 +152,9 @@ __global__ void __launch_bounds__(256) k_update32(JacStepArgs a, float* __restri
 }
 
 // ----------------------------------------------------------------------------- FP64 GEMM
-// C = op(A) * diag(sb) * B - diag(dsub)  (FP64 mma m16n8k16), column-major, C is Mr x Nc.
+// C = op(A) * diag(sb) * op(B) - diag(dsub)  (FP64 mma m16n8k16), column-major, C is Mr x Nc;
+// blockIdx.z selects a batch member at element strides sa, sbb, sc.
+//   transB = 1: op(B)[r][j] = B[r * ldb + j]; else B[j * ldb + r].
 //   transA = 1: op(A)[i][r] = A[i * lda + r]  (A stored K x Mr: C = A^T B)
 //   transA = 0: op(A)[i][r] = A[r * lda + i]  (A stored Mr x K)
 //   sb: optional +-1 per r (row signs of B); dsub: optional, subtracted on the diagonal.
@@ -163,9 +165,13 @@ __global__ void __launch_bounds__(256) k_update32(JacStepArgs a, float* __restri
 __global__ void __launch_bounds__(128) k_gemm64(int Mr, int Nc, int K, const double* __restrict__ A, int lda,
                                                int transA, const double* __restrict__ B, int ldb,
                                                const int8_t* __restrict__ sb, const int8_t* __restrict__ dsub,
-                                               double* __restrict__ C, int ldc, int sym) {
+                                               double* __restrict__ C, int ldc, int sym, int transB, long long sa,
+                                               long long sbb, long long sc) {
   __shared__ __align__(16) double As[DG_T * DG_LD];  // [i][r]
   __shared__ __align__(16) double Bs[DG_T * DG_LD];  // [j][r]
+  A += (size_t)blockIdx.z * sa;
+  B += (size_t)blockIdx.z * sbb;
+  C += (size_t)blockIdx.z * sc;
   const int bi = blockIdx.x, bj = blockIdx.y;
   if (sym && bj < bi) return;
   const int i0 = bi * DG_T, j0 = bj * DG_T;
@@ -187,12 +193,18 @@ __global__ void __launch_bounds__(128) k_gemm64(int Mr, int Nc, int K, const dou
         if (i0 + i < Mr && k0 + r < K) va = A[(size_t)(k0 + r) * lda + i0 + i];
       }
       As[i * DG_LD + r] = va;
-      const int rb = idx % DG_T, jb = idx / DG_T;
+      int rb, jb;
       double vb = 0.0;
-      if (j0 + jb < Nc && k0 + rb < K) {
-        vb = B[(size_t)(j0 + jb) * ldb + k0 + rb];
-        if (sb && sb[k0 + rb] < 0) vb = -vb;
+      if (transB) {  // op(B)[r][j] = B[r * ldb + j]
+        jb = idx % DG_T;
+        rb = idx / DG_T;
+        if (j0 + jb < Nc && k0 + rb < K) vb = B[(size_t)(k0 + rb) * ldb + j0 + jb];
+      } else {
+        rb = idx % DG_T;
+        jb = idx / DG_T;
+        if (j0 + jb < Nc && k0 + rb < K) vb = B[(size_t)(j0 + jb) * ldb + k0 + rb];
       }
+      if (sb && k0 + rb < K && sb[k0 + rb] < 0) vb = -vb;
       Bs[jb * DG_LD + rb] = vb;
     }
     __syncthreads();
@@ -303,6 +315,25 @@ __global__ void k_absmax64(int n, const double* __restrict__ M, int ldm, unsigne
   }
   mloc = warp_max_d(mloc);
   if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(mloc));
+}
+
+// FP32 copies <-> FP64 working arrays of every problem (same layouts: Gw/G32 ld mp, Vw/V32 ld np).
+// to64 = 0: G32 = Gw, V32 = Vw (rounded); to64 = 1: Gw = G32, Vw = V32.  Grid (blocks, nprob).
+__global__ void k_lowp_copy(const JacProb* __restrict__ probs, int to64) {
+  const JacProb& a = probs[blockIdx.y];
+  if (!a.G32) return;
+  const size_t ng = (size_t)a.mp * a.n;
+  const size_t nv = (a.V32 && a.Vw) ? (size_t)a.np * a.n : 0;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < ng + nv; e += (size_t)gridDim.x * blockDim.x) {
+    if (e < ng) {
+      if (to64) a.Gw[e] = (double)a.G32[e];
+      else a.G32[e] = (float)a.Gw[e];
+    } else {
+      const size_t f = e - ng;
+      if (to64) a.Vw[f] = (double)a.V32[f];
+      else a.V32[f] = (float)a.Vw[f];
+    }
+  }
 }
 
 }  // namespace jac

@@ -1,9 +1,9 @@
 // gram_update.cu -- the two dense contractions of a parallel step (Sec. 2.3):
 //   gram:   A_P = [G_p G_q]^* [G_p G_q]                    (Eq. (3.4))
 //   update: [G_p G_q] <- [G_p G_q] V_P,  [V_p V_q] <- [V_p V_q] V_P   (Algorithm 3.4)
-// Both run on the FP64 tensor path (mma.sync m16n8k16 f64), which on GB300 is ~4x the FP64
-// FFMA rate.  The pairs of a step are disjoint, so every CTA owns its columns and the update
-// is in place.
+// Both run on the FP64 tensor path (mma.sync m16n8k16 f64).  The pairs of a step are disjoint,
+// so every CTA owns its columns and the update is in place.  Problems of a batch are indexed by
+// grid dimension y (gram, pivot) or z (update).
 #include <cooperative_groups.h>
 
 #include "jacobi_common.cuh"
@@ -20,21 +20,22 @@ namespace jac {
 
 __device__ __forceinline__ int pair_col(int c, int wp, int op, int oq) { return c < wp ? op + c : oq + (c - wp); }
 
-// Grid: half * CS CTAs, cluster (CS,1,1): the CS CTAs of a cluster share one pair and split
+// Grid (half * CS, nprob), cluster (CS,1,1): the CS CTAs of a cluster share one pair and split
 // its rows; their k x k partial sums are added through distributed shared memory, each CTA
-// reducing and storing 1/CS of the entries.  Output Ap[pair] is KMAX x KMAX (k x k used),
-// symmetric, stored column-major.
-__global__ void __launch_bounds__(128) k_gram(JacStepArgs a, const int* __restrict__ step_pairs,
-                                             const int* __restrict__ step_count, int CS,
-                                             double* __restrict__ Ap) {
+// reducing and storing 1/CS of the entries.  Output Ap[pair] (ld apld, k x k used), symmetric,
+// column-major.
+__global__ void __launch_bounds__(128) k_gram(const JacProb* __restrict__ probs, int s, int CS) {
   extern __shared__ __align__(16) double gsm[];
   double* Xs = gsm;                                  // [KMAX cols][GRAM_LDS rows]
   double* Cs = gsm + JAC_KMAX * GRAM_LDS;            // [KMAX][GRAM_LDC]
   cg::cluster_group cluster = cg::this_cluster();
+  const JacProb& a = probs[blockIdx.y];
   const int pair = blockIdx.x / CS;
   const int crank = (int)cluster.block_rank();
-  if (pair >= *step_count) return;  // uniform over the cluster: no cluster barrier is pending
-  const int p = step_pairs[2 * pair], q = step_pairs[2 * pair + 1];
+  // uniform over the cluster: no cluster barrier is pending
+  if (!a.active || s >= a.nsteps || pair >= a.counts[s]) return;
+  const int* sp = a.pairs + (size_t)s * a.half * 2;
+  const int p = sp[2 * pair], q = sp[2 * pair + 1];
   const int op = a.boff[p], wp = a.boff[p + 1] - op, oq = a.boff[q], wq = a.boff[q + 1] - oq;
   const int k = wp + wq, KP = (k + 15) & ~15;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
@@ -66,6 +67,7 @@ __global__ void __launch_bounds__(128) k_gram(JacStepArgs a, const int* __restri
         const int tile = warp + 4 * u;
         if (tile < ntiles) {
           const int ti = tile / ntj, tj = tile % ntj;
+          if (8 * tj + 7 < 16 * ti) continue;  // strictly below the diagonal: mirrored later
           double av[8], bv[4];
           const double* xa0 = Xs + (16 * ti + g) * GRAM_LDS + kk + 4 * t;
           const double* xa1 = xa0 + 8 * GRAM_LDS;
@@ -82,17 +84,23 @@ __global__ void __launch_bounds__(128) k_gram(JacStepArgs a, const int* __restri
       }
     }
   }
-  // partial -> own shared memory
+  // partial -> own shared memory (upper tiles and their mirror)
 #pragma unroll
   for (int u = 0; u < 8; ++u) {
     const int tile = warp + 4 * u;
     if (tile < ntiles) {
       const int ti = tile / ntj, tj = tile % ntj;
-      const int r = 16 * ti + g, c = 8 * tj + 2 * t;
-      Cs[r * GRAM_LDC + c] = acc[u][0];
-      Cs[r * GRAM_LDC + c + 1] = acc[u][1];
-      Cs[(r + 8) * GRAM_LDC + c] = acc[u][2];
-      Cs[(r + 8) * GRAM_LDC + c + 1] = acc[u][3];
+      if (8 * tj + 7 < 16 * ti) continue;
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const int r = 16 * ti + g + 8 * (v >> 1), c = 8 * tj + 2 * t + (v & 1);
+        // each entry written once: (r, c) with c >= r and its mirror; (r, c) with c < r of a
+        // tile crossing the diagonal comes from the tile holding (c, r)
+        if (c >= r) {
+          Cs[r * GRAM_LDC + c] = acc[u][v];
+          Cs[c * GRAM_LDC + r] = acc[u][v];
+        }
+      }
     }
   }
   cluster.sync();
@@ -100,33 +108,32 @@ __global__ void __launch_bounds__(128) k_gram(JacStepArgs a, const int* __restri
   const int tot = k * k;
   const int per = (tot + CS - 1) / CS;
   const int e0 = crank * per, e1 = min(tot, e0 + per);
-  double* out = Ap + (size_t)pair * JAC_KMAX * JAC_KMAX;
+  double* out = a.Ap + (size_t)pair * a.apld * a.apld;
   for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
     const int i = e % k, j = e / k;
-    double s = 0.0;
+    double sum = 0.0;
     for (int rk = 0; rk < CS; ++rk) {
       const double* rc = cluster.map_shared_rank(Cs, rk);
-      s += rc[i * GRAM_LDC + j];
+      sum += rc[i * GRAM_LDC + j];
     }
-    out[j * JAC_KMAX + i] = s;
+    out[j * a.apld + i] = sum;
   }
   cluster.sync();  // keep every partial alive until all remote reads are done
 }
 
-// Grid: (half, nslab); slab y covers 64 rows of Gw (y < gslabs) or of Vw.  128 threads.
+// Grid (half, nslab, nprob); slab y covers 64 rows of Gw (y < gslabs) or of Vw.  128 threads.
 // Y = X V_P with X the slab (64 x k), V_P (k x k) from the pivot kernel; written in place.
 #define UPD_RS 64
 #define UPD_LD (JAC_KMAX + 2)
-__global__ void __launch_bounds__(128) k_update(JacStepArgs a, const int* __restrict__ step_pairs,
-                                               const int* __restrict__ step_count,
-                                               const double* __restrict__ vp, const int* __restrict__ skip,
-                                               int gslabs) {
+__global__ void __launch_bounds__(128) k_update(const JacProb* __restrict__ probs, int s, int gslabs) {
   extern __shared__ __align__(16) double usm[];
   double* Bs = usm;                       // V_P: [col j][UPD_LD] (k index contiguous)
   double* Xs = usm + JAC_KMAX * UPD_LD;   // X slab row-major: [row][UPD_LD]
+  const JacProb& a = probs[blockIdx.z];
   const int pair = blockIdx.x;
-  if (pair >= *step_count || skip[pair]) return;
-  const int p = step_pairs[2 * pair], q = step_pairs[2 * pair + 1];
+  if (!a.active || s >= a.nsteps || pair >= a.counts[s] || a.skip[pair]) return;
+  const int* sp = a.pairs + (size_t)s * a.half * 2;
+  const int p = sp[2 * pair], q = sp[2 * pair + 1];
   const int op = a.boff[p], wp = a.boff[p + 1] - op, oq = a.boff[q], wq = a.boff[q + 1] - oq;
   const int k = wp + wq, KP = (k + 15) & ~15;
   double* base;
@@ -137,6 +144,7 @@ __global__ void __launch_bounds__(128) k_update(JacStepArgs a, const int* __rest
     r0 = blockIdx.y * UPD_RS;
     rs = min(UPD_RS, a.mp - r0);
   } else {
+    if (!a.Vw) return;
     base = a.Vw;
     ld = a.np;
     r0 = (blockIdx.y - gslabs) * UPD_RS;
@@ -144,10 +152,10 @@ __global__ void __launch_bounds__(128) k_update(JacStepArgs a, const int* __rest
   }
   if (rs <= 0) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  const double* V = vp + (size_t)pair * JAC_KMAX * JAC_KMAX;
+  const double* V = a.vp + (size_t)pair * a.apld * a.apld;
   for (int idx = threadIdx.x; idx < KP * KP; idx += blockDim.x) {
     const int c = idx % KP, j = idx / KP;  // V_P[c][j], column-major source
-    Bs[j * UPD_LD + c] = (c < k && j < k) ? V[j * JAC_KMAX + c] : 0.0;
+    Bs[j * UPD_LD + c] = (c < k && j < k) ? V[j * a.apld + c] : 0.0;
   }
   for (int idx = threadIdx.x; idx < KP * rs; idx += blockDim.x) {
     const int r = idx % rs, c = idx / rs;

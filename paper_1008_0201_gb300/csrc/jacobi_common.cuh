@@ -1,7 +1,7 @@
 // jacobi_common.cuh -- shared device helpers and internal types of the GB300 Jacobi library.
 //
 // Arithmetic placement on GB300 (measured on the target: FP64 FFMA ~1.0 TFLOP/s, mma.sync
-// m16n8k16 f64 ~4.2 TFLOP/s, FP32 FFMA ~74 TFLOP/s, FP64 sqrt/div ~650 cycles latency):
+// m16n8k16 f64 ~1.0 TFLOP/s, FP32 FFMA ~74 TFLOP/s, FP64 sqrt/div ~650 cycles latency):
 //   - every FP64 contraction (pivot Gram block, block update, J-orthogonalization of V_P)
 //     runs on the FP64 tensor path, mma.sync.m16n8k16.f64;
 //   - the 2x2 rotation angles are computed in FP32 on a shifted representation that keeps
@@ -53,6 +53,22 @@ __device__ __forceinline__ double warp_max_d(double v) {
   return v;
 }
 
+// Inner step s of the circle (round-robin) ordering on kk (even) positions, position kk-1 fixed:
+// the pair (li < lj) of slot w.
+__device__ __forceinline__ void rr_inner_pair(int kk, int s, int w, int& li, int& lj) {
+  const int L = kk - 1;
+  if (w == 0) {
+    li = s;
+    lj = kk - 1;
+  } else {
+    int x = s + w, y = s - w;
+    if (x >= L) x -= L;
+    if (y < 0) y += L;
+    li = min(x, y);
+    lj = max(x, y);
+  }
+}
+
 __device__ __forceinline__ int warp_sum_i(int v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -62,25 +78,54 @@ __device__ __forceinline__ int warp_sum_i(int v) {
 }  // namespace jac
 
 // ------------------------------------------------------------------ internal problem view
-// Internal layout: Gw is (mp x n) column-major, ld = mp = m rounded up to 16 with zero rows;
-// columns are sorted so that J = diag(I_npos, -I).  Vw is (np x n), np = n rounded up to 16.
-// Block b spans columns [boff[b], boff[b+1]).
-struct JacStepArgs {
-  double* Gw;
-  int mp;            // rows of Gw (multiple of 16), also its ld
-  double* Vw;        // NULL if V is not accumulated
-  int np;            // rows of Vw (multiple of 16), also its ld
-  int n;
-  int nb;
+// One problem of a batch (a single solve is a batch of one).  Internal layout: Gw is (mp x n)
+// column-major, ld = mp = m rounded up to 16 with zero rows; columns are sorted so that
+// J = diag(I_npos, -I).  Vw is (np x n), np = n rounded up to 16, rows in input order.  Block b
+// spans columns [boff[b], boff[b+1]).  The step kernels take an array of these and a step index
+// s, and index the problem by a grid dimension; a problem with active = 0 is skipped.
+struct JacProb {
+  double* Gw;        // FP64 factor
+  double* Vw;        // FP64 V (NULL if not accumulated)
+  float* G32;        // FP32 copies used by the FP32 sweeps (NULL otherwise)
+  float* V32;
+  int mp, np, n, nb, half, nsteps;
   const int* boff;   // [nb+1]
   const int8_t* Js;  // [n] internal (sorted) signs
-  const int* pairs;  // [steps][half][2]
-  const int* counts; // [steps]
-  int half;          // nb/2
+  const int* pairs;  // [nsteps][half][2]
+  const int* counts; // [nsteps]
+  double* Ap;        // [half][apld * apld] Gram blocks
+  double* vp;        // [half][apld * apld] pivot transforms V_P
+  int apld;          // leading dimension of a pivot block (the pivot capacity of its class)
+  int active;        // 0: converged or failed, every kernel skips the problem
+  int* skip;         // [half]
+  struct PairStat* stats;  // [nsteps][half]
+  unsigned* pflags;  // JAC_DEVERR_* bits of this problem
 };
 
+// User-side buffers of one problem and its finalize scratch.
+struct JacIO {
+  double* G;           // user factor (device), m x n, read at set-up and overwritten at the end
+  int ldg, m;
+  const int8_t* J;     // user signs (device), NULL for J = I
+  int* perm_in;        // [n] internal column c holds input column perm_in[c]
+  double* lambda;      // [n]
+  double* U;           // may be NULL
+  int ldu;
+  double* V;           // may be NULL
+  int ldv;
+  double* nrm2;        // [n] scratch
+  double* lam;         // [n] scratch
+  int* rank;           // [n] scratch
+  int flags;           // bit 0: non-finite input, bit 1: invalid sign entry
+  int sweeps;          // sweeps run while active
+  long long rotations;
+};
+
+struct PairStat;
 struct PivotParams {
-  double tol;        // outer rotation threshold
+  double tol;        // outer rotation threshold; <= 0: max(n, tol_m sqrt(mp)) tol_eps for a problem
+  double tol_eps;    // of order n with mp (padded) rows: the FP32 Gram resolves no less than ~eps sqrt(m)
+  double tol_m;
   int factor;        // 0 unpivoted, 2 sign-pivoted
   int ns_mode;       // 1: make V_P J-unitary in FP64 (Newton-Schulz); 0: leave the FP32 transform
 };

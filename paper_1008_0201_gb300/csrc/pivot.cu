@@ -28,104 +28,111 @@
 
 namespace jac {
 
-#define PV_KM JAC_KMAX
-#define PV_LDF JAC_KMAX        // F, W column stride (floats): column c rows 2l, 2l+1 in lane l
-#define PV_LDS (JAC_KMAX + 1)  // Cholesky working matrix / FP32 scratch stride (floats)
-#define PV_LDV (JAC_KMAX + 1)  // FP64 V / M stride
-#define PV_THREADS 1024
-#define PV_WARPS 32
-
+// Pivot capacity KM (largest k = w_p + w_q of the class), KM / 32 rows of a column per lane,
+// KM / 2 warps (one column pair each).
+template <int KM>
 struct PivotSmem {
-  double V[PV_KM * PV_LDV];   // A_P first, then V (physical coordinates), FP64
-  double M[PV_KM * PV_LDV];   // FP64 residual
-  float S[PV_KM * PV_LDS];    // Cholesky working matrix, later FP32 J M
-  float F[PV_KM * PV_LDF];
-  float W[PV_KM * PV_LDF];
-  float Vf[PV_KM * PV_LDS];   // FP32 copy of V for the correction product
-  float cn[PV_KM];            // tracked c_i = ||r_i||^2 - s_i^2 of the inner sweep
-  double invd[PV_KM];
-  float dd[PV_KM];
-  float fid[PV_KM];           // fp32(1 / d_i)
-  int perm[PV_KM];
-  int lpos[PV_KM];
-  int jphys[PV_KM];
-  int jloc[PV_KM];
-  float red_f[PV_WARPS][4];
-  int red_i[PV_WARPS][2];
-  float4 rotp[PV_WARPS];      // rotation of pair w in the current inner step: q11, q12, q21, ch-1
-  int rflag[PV_WARPS];
-  float sijv[PV_WARPS];
+  static constexpr int LDF = KM;       // F, W column stride (floats)
+  static constexpr int LDS = KM + 1;   // Cholesky matrix / FP32 scratch stride (floats)
+  static constexpr int LDV = KM + 1;   // FP64 V / M stride
+  static constexpr int NW = KM / 2;
+  double V[KM * LDV];   // A_P first, then V (physical coordinates), FP64
+  double M[KM * LDV];   // FP64 residual
+  float S[KM * LDS];    // Cholesky working matrix (upper triangle), later FP32 J M
+  float F[KM * LDF];
+  float W[KM * LDF];
+  float Vf[KM * LDS];   // FP32 copy of V for the correction product
+  float cn[KM];         // tracked c_i = ||r_i||^2 - s_i^2 of the inner sweep
+  float dd[KM];
+  float fid[KM];        // fp32(1 / d_i)
+  int perm[KM];
+  int lpos[KM];
+  int jphys[KM];
+  int jloc[KM];
+  float red_f[NW][4];
+  int red_i[NW][2];
+  float4 rotp[NW];      // rotation of pair w in the current inner step: q11, q12, q21, q11-1
+  int rflag[NW];
+  float sijv[NW];
+  double trs[2];
   int piv;
   int bad;
 };
 
-union F2U {
-  float2 f;
-  unsigned long long u;
+// a column slice held by one lane: rows lane*R .. lane*R + R - 1
+template <int R>
+struct Slice {
+  float v[R];
 };
 
-// packed FP32 pair arithmetic (Blackwell f32x2 pipe)
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
-  F2U A, B, C, D;
-  A.f = a;
-  B.f = b;
-  C.f = c;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(D.u) : "l"(A.u), "l"(B.u), "l"(C.u));
-  return D.f;
-}
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
-  F2U A, B, D;
-  A.f = a;
-  B.f = b;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(D.u) : "l"(A.u), "l"(B.u));
-  return D.f;
-}
-
-__device__ __forceinline__ void rr_inner_pair(int kk, int s, int w, int& li, int& lj) {
-  // circle method on kk (even) positions: position kk-1 fixed
-  const int L = kk - 1;
-  if (w == 0) {
-    li = s;
-    lj = kk - 1;
+template <int R>
+__device__ __forceinline__ Slice<R> load_slice(const float* col, int lane) {
+  Slice<R> x;
+  if (R == 2) {
+    const float2 t = reinterpret_cast<const float2*>(col)[lane];
+    x.v[0] = t.x;
+    x.v[R - 1] = t.y;
   } else {
-    int x = (s + w) % L, y = (s - w + L) % L;
-    li = min(x, y);
-    lj = max(x, y);
+    x.v[0] = col[lane];
   }
+  return x;
 }
 
-__device__ __forceinline__ float block_max_f(float v, PivotSmem& sm, int slot) {
+template <int R>
+__device__ __forceinline__ void store_slice(float* col, int lane, const Slice<R>& x) {
+  if (R == 2)
+    reinterpret_cast<float2*>(col)[lane] = make_float2(x.v[0], x.v[R - 1]);
+  else
+    col[lane] = x.v[0];
+}
+
+template <int KM>
+__device__ __forceinline__ float block_max_f(float v, PivotSmem<KM>& sm, int slot) {
+  constexpr int NW = KM / 2;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
   if (lane == 0) sm.red_f[warp][slot] = v;
   __syncthreads();
   float r = 0.0f;
-  for (int w = 0; w < PV_WARPS; ++w) r = fmaxf(r, sm.red_f[w][slot]);
+  for (int w = 0; w < NW; ++w) r = fmaxf(r, sm.red_f[w][slot]);
   __syncthreads();
   return r;
 }
 
-__global__ void __launch_bounds__(PV_THREADS, 1)
-    k_pivot(JacStepArgs a, const int* __restrict__ step_pairs, const int* __restrict__ step_count,
-            const double* __restrict__ Ap, PivotParams pp, double* __restrict__ vp, int* __restrict__ skip,
-            PairStat* __restrict__ stats, unsigned* __restrict__ err) {
+template <int KM>
+__global__ void __launch_bounds__(KM * 16, 1)
+    k_pivot(const JacProb* __restrict__ probs, int s, PivotParams pp) {
+  constexpr int NT = KM * 16, NW = KM / 2, R = KM / 32;
+  using SM = PivotSmem<KM>;
+  constexpr int LDF = SM::LDF, LDS = SM::LDS, LDV = SM::LDV;
   extern __shared__ __align__(16) unsigned char pv_raw[];
-  PivotSmem& sm = *reinterpret_cast<PivotSmem*>(pv_raw);
+  SM& sm = *reinterpret_cast<SM*>(pv_raw);
+  const JacProb& a = probs[blockIdx.y];
+  unsigned* err = a.pflags;
   const int pair = blockIdx.x;
-  if (pair >= *step_count) return;
+  if (!a.active || s >= a.nsteps || pair >= a.counts[s]) return;
+  PairStat* stats = a.stats + (size_t)s * a.half;
   const long long t_start = clock64();
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int p = step_pairs[2 * pair], q = step_pairs[2 * pair + 1];
+  const int* sp = a.pairs + (size_t)s * a.half * 2;
+  const int p = sp[2 * pair], q = sp[2 * pair + 1];
   const int op = a.boff[p], wp = a.boff[p + 1] - op, oq = a.boff[q], wq = a.boff[q + 1] - oq;
   const int k = wp + wq, KP = (k + 15) & ~15;
   double* Vs = sm.V;
+  if (k > KM) {  // the driver assigns classes by k; reported, never trapped
+    if (tid == 0) {
+      atomicOr(err, JAC_DEVERR_INNER_LIMIT);
+      a.skip[pair] = 1;
+    }
+    return;
+  }
 
   // ---- 1. load A_P, scaled matrix E, statistics ----------------------------------------------
-  const double* A = Ap + (size_t)pair * JAC_KMAX * JAC_KMAX;
-  for (int e = tid; e < k * k; e += PV_THREADS) {
+  const double* A = a.Ap + (size_t)pair * a.apld * a.apld;
+  for (int e = tid; e < k * k; e += NT) {
     const int i = e % k, j = e / k;
-    Vs[j * PV_LDV + i] = A[j * JAC_KMAX + i];
+    Vs[j * LDV + i] = A[j * a.apld + i];
   }
   if (tid == 0) sm.bad = 0;
   __syncthreads();
@@ -133,19 +140,18 @@ __global__ void __launch_bounds__(PV_THREADS, 1)
   if (tid < k) {
     const int col = tid < wp ? op + tid : oq + (tid - wp);
     sm.jloc[tid] = a.Js[col];
-    const double aii = Vs[tid * PV_LDV + tid];
+    const double aii = Vs[tid * LDV + tid];
     if (!(aii > 0.0) || !(aii < 1.0e300)) atomicOr(&sm.bad, 1);
     const float d = sqrtf((float)aii);
     const double id = 1.0 / (double)d;
     sm.dd[tid] = d;
-    sm.invd[tid] = id;
     sm.fid[tid] = (float)id;
     sm.perm[tid] = tid;
     // e_ii = a_ii / d_i^2 - 1 in FP64 (cancellation), then rounded once
-    sm.S[tid * PV_LDS + tid] = (float)(aii * id * id - 1.0);
+    sm.S[tid * LDS + tid] = (float)(aii * id * id - 1.0);
     tr = aii;
   }
-  for (int e = tid; e < PV_KM * PV_LDF; e += PV_THREADS) {
+  for (int e = tid; e < KM * LDF; e += NT) {
     sm.F[e] = 0.0f;
     sm.W[e] = 0.0f;
   }
@@ -153,7 +159,7 @@ __global__ void __launch_bounds__(PV_THREADS, 1)
   if (sm.bad) {
     if (tid == 0) {
       atomicOr(err, JAC_DEVERR_NOTPD);
-      skip[pair] = 1;
+      a.skip[pair] = 1;
       PairStat st = {};
       stats[pair] = st;
     }
@@ -162,22 +168,23 @@ __global__ void __launch_bounds__(PV_THREADS, 1)
   // off-diagonal e_ij = a_ij / (d_i d_j) in FP32: it is the scaled off-diagonal entry
   // |a_ij| / sqrt(a_ii a_jj) to FP32 accuracy, so it drives the statistics; only entries within
   // 2^-12 of the threshold are re-decided in FP64.
-  const float tolf = (float)pp.tol;
+  const double tol = pp.tol > 0.0 ? pp.tol : fmax((double)a.n, pp.tol_m * sqrt((double)a.mp)) * pp.tol_eps;
+  const float tolf = (float)tol;
   float mx = 0.0f, oc = 0.0f, od = 0.0f;
   int cnt = 0;
-  for (int e = tid; e < k * k; e += PV_THREADS) {
+  for (int e = tid; e < k * k; e += NT) {
     const int i = e % k, j = e / k;
     if (i == j) continue;
-    const float aij = (float)Vs[j * PV_LDV + i];
+    const float aij = (float)Vs[j * LDV + i];
     const float eij = aij * sm.fid[i] * sm.fid[j];
-    sm.S[j * PV_LDS + i] = eij;
+    sm.S[j * LDS + i] = eij;
     if (i < j) {
       const float r = fabsf(eij);
       mx = fmaxf(mx, r);
       bool hit = r > tolf;
       if (fabsf(r - tolf) <= tolf * 2.44140625e-4f) {
-        const double ad = Vs[j * PV_LDV + i];
-        hit = ad * ad > pp.tol * pp.tol * Vs[i * PV_LDV + i] * Vs[j * PV_LDV + j];
+        const double ad = Vs[j * LDV + i];
+        hit = ad * ad > tol * tol * Vs[i * LDV + i] * Vs[j * LDV + j];
       }
       cnt += hit ? 1 : 0;
       const float a2 = aij * aij;
@@ -197,12 +204,12 @@ __global__ void __launch_bounds__(PV_THREADS, 1)
     sm.red_f[warp][1] = oc;
     sm.red_f[warp][2] = od;
     sm.red_i[warp][0] = cnt;
-    if (warp < 2) sm.M[warp] = tr;
+    if (warp < 2) sm.trs[warp] = tr;
   }
   __syncthreads();
   mx = oc = od = 0.0f;
   cnt = 0;
-  for (int w = 0; w < PV_WARPS; ++w) {
+  for (int w = 0; w < NW; ++w) {
     mx = fmaxf(mx, sm.red_f[w][0]);
     oc += sm.red_f[w][1];
     od += sm.red_f[w][2];
@@ -212,7 +219,7 @@ __global__ void __launch_bounds__(PV_THREADS, 1)
   st.max_scaled = (double)mx;
   st.off2_cross = (double)oc;
   st.off2_diag = (double)od;
-  st.trace = sm.M[0] + sm.M[1];
+  st.trace = sm.trs[0] + ((NW > 1 && k > 32) ? sm.trs[1] : 0.0);
   st.rotations = 0;
   st.inner_sweeps = 0;
   st.ns_steps = 0;
@@ -220,7 +227,7 @@ __global__ void __launch_bounds__(PV_THREADS, 1)
   const long long t_stats = clock64();
   if (cnt == 0) {
     if (tid == 0) {
-      skip[pair] = 1;
+      a.skip[pair] = 1;
       st.cyc[0] = t_stats - t_start;
       st.cyc[1] = st.cyc[2] = st.cyc[3] = 0;
       stats[pair] = st;
@@ -236,7 +243,7 @@ __global__ void __launch_bounds__(PV_THREADS, 1)
   __syncthreads();
   const bool signpiv = (pp.factor == 2);
   // S holds the trailing matrix in its upper triangle: U(a, b) = S[max(a,b) * LDS + min(a,b)]
-  const int cx = tid & 63, cy = tid >> 6;  // trailing update: column cx, rows i + 1 + cy + 16 u <= cx
+  const int cx = tid % KM, cy = tid / KM;  // trailing update: column cx, rows i + 1 + cy + 16 u <= cx
   for (int i = 0; i < k; ++i) {
     if (signpiv) {
       // pivot: the largest unscaled Schur diagonal d_j^2 (1 + s_jj) in the sign group of step i
@@ -246,7 +253,7 @@ __global__ void __launch_bounds__(PV_THREADS, 1)
         int bj = i;
         for (int j = i + lane; j < hi; j += 32) {
           const float dj = sm.dd[j];
-          const float v = dj * dj * (1.0f + sm.S[j * PV_LDS + j]);
+          const float v = dj * dj * (1.0f + sm.S[j * LDS + j]);
           if (v > best) {
             best = v;
             bj = j;
@@ -268,24 +275,24 @@ __global__ void __launch_bounds__(PV_THREADS, 1)
       if (pv != i) {  // uniform
         // symmetric swap of rows/columns i and pv of the trailing matrix (upper storage), of
         // the computed rows of F (columns i and pv), and of the bookkeeping
-        for (int tt = tid; tt < k; tt += PV_THREADS) {
+        for (int tt = tid; tt < k; tt += NT) {
           if (tt > i && tt != pv) {
-            const int a1 = (tt > i) ? tt * PV_LDS + i : i * PV_LDS + tt;
-            const int a2 = (tt > pv) ? tt * PV_LDS + pv : pv * PV_LDS + tt;
+            const int a1 = tt * LDS + i;
+            const int a2 = (tt > pv) ? tt * LDS + pv : pv * LDS + tt;
             const float x = sm.S[a1];
             sm.S[a1] = sm.S[a2];
             sm.S[a2] = x;
           }
           if (tt < i) {
-            const float x = sm.F[i * PV_LDF + tt];
-            sm.F[i * PV_LDF + tt] = sm.F[pv * PV_LDF + tt];
-            sm.F[pv * PV_LDF + tt] = x;
+            const float x = sm.F[i * LDF + tt];
+            sm.F[i * LDF + tt] = sm.F[pv * LDF + tt];
+            sm.F[pv * LDF + tt] = x;
           }
         }
         if (tid == 0) {
-          float x = sm.S[i * PV_LDS + i];
-          sm.S[i * PV_LDS + i] = sm.S[pv * PV_LDS + pv];
-          sm.S[pv * PV_LDS + pv] = x;
+          float x = sm.S[i * LDS + i];
+          sm.S[i * LDS + i] = sm.S[pv * LDS + pv];
+          sm.S[pv * LDS + pv] = x;
           int y = sm.perm[i];
           sm.perm[i] = sm.perm[pv];
           sm.perm[pv] = y;
@@ -299,39 +306,40 @@ __global__ void __launch_bounds__(PV_THREADS, 1)
         __syncthreads();
       }
     }
-    const float sii = sm.S[i * PV_LDS + i];
+    const float sii = sm.S[i * LDS + i];
     const float piv1 = 1.0f + sii;
     // The scaled Schur pivot is 1 / (A~^-1)_ii >= 1 / kappa(A~).  Below 64 eps_32 the column is
-    // in the span of the previous ones at the precision of this factorization: the block (and
-    // G) is treated as rank deficient.
+    // in the span of the previous ones at the precision of this factorization: the block goes
+    // to the FP64 pivot kernel (which tells an ill-conditioned block from a singular one).
     if (!(piv1 > 3.8146973e-6f)) {
       if (tid == 0) sm.bad = 1;
       break;  // uniform: every thread read the same sii
     }
     const float r = sqrtf(piv1), ipiv = 1.0f / piv1;
     // row i of F~ and the trailing update read only row i of S, which this step does not write
-    if (cy == 0 && cx > i && cx < k) sm.F[cx * PV_LDF + i] = sm.S[cx * PV_LDS + i] / r;
-    if (tid == 0) sm.F[i * PV_LDF + i] = sii / (1.0f + r);
+    if (cy == 0 && cx > i && cx < k) sm.F[cx * LDF + i] = sm.S[cx * LDS + i] / r;
+    if (tid == 0) sm.F[i * LDF + i] = sii / (1.0f + r);
     if (cx > i && cx < k) {
-      const float sil = sm.S[cx * PV_LDS + i] * ipiv;
-      for (int jj = i + 1 + cy; jj <= cx; jj += PV_THREADS / 64)
-        sm.S[cx * PV_LDS + jj] -= sil * sm.S[jj * PV_LDS + i];
+      const float sil = sm.S[cx * LDS + i] * ipiv;
+      for (int jj = i + 1 + cy; jj <= cx; jj += NT / KM) sm.S[cx * LDS + jj] -= sil * sm.S[jj * LDS + i];
     }
     __syncthreads();
   }
   __syncthreads();
-  if (sm.bad) {
+  if (sm.bad) {  // handed over to the FP64 pivot kernel, which decides on rank deficiency
     if (tid == 0) {
-      atomicOr(err, JAC_DEVERR_NOTPD);
-      skip[pair] = 1;
+      a.skip[pair] = 2;
+      st.cyc[0] = t_stats - t_start;
+      st.cyc[1] = clock64() - t_stats;
+      st.cyc[2] = st.cyc[3] = 0;
       stats[pair] = st;
     }
     return;
   }
   // R = Dp + F: scale the columns of F~ by dd; logical order of the inner sweep
-  for (int e = tid; e < k * k; e += PV_THREADS) {
+  for (int e = tid; e < k * k; e += NT) {
     const int r = e % k, c = e / k;
-    if (r <= c) sm.F[c * PV_LDF + r] *= sm.dd[c];
+    if (r <= c) sm.F[c * LDF + r] *= sm.dd[c];
   }
   if (tid < k) {
     const int l = tid;
@@ -345,105 +353,105 @@ __global__ void __launch_bounds__(PV_THREADS, 1)
   // FP32), at least the FP32 noise level of the shifted dot products
   const float tol_in = fmaxf(0.5f * tolf, 64.0f * 5.9604645e-8f * mx);
   const int kk = k + (k & 1);
-  float2* F2 = reinterpret_cast<float2*>(sm.F);
-  float2* W2 = reinterpret_cast<float2*>(sm.W);
   // Each inner step runs in three phases separated by barriers:
   //   A: warp w forms the dot product r_i^T r_j of its pair (shifted: F_i^T F_j);
   //   B: warp 0, lane l, forms the rotation of pair l from a_ii, a_jj, a_ij: the scalar 2x2
-  //      work of all pairs shares one instruction stream instead of 32 redundant ones;
+  //      work of all pairs shares one instruction stream instead of one per warp;
   //   C: warp w applies its rotation to the columns of F and W.
   int total_rot = 0, inner = 0;
   const int P = kk / 2;
   for (inner = 0; inner < JAC_INNER_MAX_SWEEPS; ++inner) {
     // c_i = 2 s_i F_ii + ||f_i||^2 recomputed at the start of every inner sweep, tracked below
-    for (int c = warp; c < k; c += PV_WARPS) {
-      const float2 f = F2[c * (PV_LDF / 2) + lane];
-      float sq = f.x * f.x + f.y * f.y;
+    for (int c = warp; c < k; c += NW) {
+      const Slice<R> f = load_slice<R>(sm.F + c * LDF, lane);
+      float sq = 0.0f;
+#pragma unroll
+      for (int u = 0; u < R; ++u) sq = fmaf(f.v[u], f.v[u], sq);
       sq = warp_sum(sq);
-      if (lane == 0) sm.cn[c] = 2.0f * sm.dd[c] * sm.F[c * PV_LDF + c] + sq;
+      if (lane == 0) sm.cn[c] = 2.0f * sm.dd[c] * sm.F[c * LDF + c] + sq;
     }
     __syncthreads();
     int my_rot = 0;       // warp 0, per lane: rotations of pair `lane` in this sweep
     float my_max = 0.0f;  // largest scaled |a_ij| rotated
-    for (int s = 0; s < kk - 1; ++s) {
+    for (int st_ = 0; st_ < kk - 1; ++st_) {
       // ---- A
       int i = 0, j = 0;
       bool act = false;
-      float2 fi = make_float2(0.f, 0.f), fj = make_float2(0.f, 0.f);
+      Slice<R> fi, fj;
       if (warp < P) {
         int li, lj;
-        rr_inner_pair(kk, s, warp, li, lj);
+        rr_inner_pair(kk, st_, warp, li, lj);
         act = lj < k;
         if (act) {
           i = sm.lpos[li];
           j = sm.lpos[lj];
-          fi = F2[i * (PV_LDF / 2) + lane];
-          fj = F2[j * (PV_LDF / 2) + lane];
-          float sij = fi.x * fj.x + fi.y * fj.y;
+          fi = load_slice<R>(sm.F + i * LDF, lane);
+          fj = load_slice<R>(sm.F + j * LDF, lane);
+          float sij = 0.0f;
+#pragma unroll
+          for (int u = 0; u < R; ++u) sij = fmaf(fi.v[u], fj.v[u], sij);
           sij = warp_sum(sij);
           if (lane == 0) sm.sijv[warp] = sij;
         }
       }
       __syncthreads();
       // ---- B
-      if (warp == 0) {
+      if (warp == 0 && lane < P) {
         int rot = 0;
         float4 rp = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (lane < P) {
-          int li, lj;
-          rr_inner_pair(kk, s, lane, li, lj);
-          if (lj < k) {
-            const int bi = sm.lpos[li], bj = sm.lpos[lj];
-            const float si = sm.dd[bi], sj = sm.dd[bj];
-            const float ci = sm.cn[bi], cj = sm.cn[bj];
-            const float aij = si * sm.F[bj * PV_LDF + bi] + sj * sm.F[bi * PV_LDF + bj] + sm.sijv[lane];
-            const float aii = fmaf(si, si, ci), ajj = fmaf(sj, sj, cj);
-            const float beta = fabsf(aij);
-            const float scaled = beta * rsqrtf(aii) * rsqrtf(ajj);
-            if (scaled > tol_in) {
-              rot = 1;
-              ++my_rot;
-              my_max = fmaxf(my_max, scaled);
-              const float e = (aij < 0.0f) ? -1.0f : 1.0f;
-              float dci, dcj;
-              if (sm.jphys[bi] == sm.jphys[bj]) {
-                // trigonometric, Eq. (2.1): cot(2 phi) = (a_jj - a_ii) / (2 |a_ij|), i.e.
-                // t = sign(a_jj - a_ii) 2|a_ij| / (|a_jj - a_ii| + sqrt((a_jj - a_ii)^2 + 4|a_ij|^2)),
-                // evaluated after an exact power-of-two scaling of both terms into [1, 4)
-                const float num = (sj - si) * (sj + si) + (cj - ci);
-                const float mxv = fmaxf(fabsf(num), 2.0f * beta);
-                const float sc = __int_as_float(0x7f000000 - (__float_as_int(mxv) & 0x7f800000));
-                const float nu = num * sc, b2 = 2.0f * beta * sc;
-                const float den = fabsf(nu) + sqrtf(fmaf(nu, nu, b2 * b2));
-                const float t = copysignf(__fdividef(b2, den), num);
-                const float c = rsqrtf(fmaf(t, t, 1.0f));
-                const float s_ = t * c;
-                rp = make_float4(c, e * s_, -e * s_, -__fdividef(s_ * s_, 1.0f + c));
-                dci = -t * beta;  // a_ii' = a_ii - t |a_ij|, a_jj' = a_jj + t |a_ij|
-                dcj = t * beta;
-              } else {
-                // hyperbolic: coth(2 phi) = -(a_ii + a_jj) / (2 |a_ij|), i.e.
-                // t = -2|a_ij| / (a_ii + a_jj + sqrt((a_ii + a_jj - 2|a_ij|)(a_ii + a_jj + 2|a_ij|))),
-                // with the |tanh| < 1 guard of Sec. 3.2
-                const float apd = aii + ajj;
-                const float sc = __int_as_float(0x7f000000 - (__float_as_int(apd) & 0x7f800000));
-                const float ap = apd * sc, b2 = 2.0f * beta * sc;
-                const float r2 = (ap - b2) * (ap + b2);
-                float t = (r2 > 0.0f) ? -__fdividef(b2, ap + sqrtf(r2)) : -1.0f;
-                if (!(fabsf(t) < 1.0f) || !((1.0f - t) * (1.0f + t) > 0.0f)) t = copysignf(0.9f, t);
-                const float ch = rsqrtf((1.0f - t) * (1.0f + t));
-                const float sh = t * ch;
-                rp = make_float4(ch, e * sh, e * sh, __fdividef(sh * sh, 1.0f + ch));
-                dci = t * beta;  // both diagonals move by t |a_ij| (the J-trace is invariant)
-                dcj = t * beta;
-              }
-              sm.cn[bi] = ci + dci;
-              sm.cn[bj] = cj + dcj;
+        int li, lj;
+        rr_inner_pair(kk, st_, lane, li, lj);
+        if (lj < k) {
+          const int bi = sm.lpos[li], bj = sm.lpos[lj];
+          const float si = sm.dd[bi], sj = sm.dd[bj];
+          const float ci = sm.cn[bi], cj = sm.cn[bj];
+          const float aij = si * sm.F[bj * LDF + bi] + sj * sm.F[bi * LDF + bj] + sm.sijv[lane];
+          const float aii = fmaf(si, si, ci), ajj = fmaf(sj, sj, cj);
+          const float beta = fabsf(aij);
+          const float scaled = beta * rsqrtf(aii) * rsqrtf(ajj);
+          if (scaled > tol_in) {
+            rot = 1;
+            ++my_rot;
+            my_max = fmaxf(my_max, scaled);
+            const float e = (aij < 0.0f) ? -1.0f : 1.0f;
+            float dci, dcj;
+            if (sm.jphys[bi] == sm.jphys[bj]) {
+              // trigonometric, Eq. (2.1): cot(2 phi) = (a_jj - a_ii) / (2 |a_ij|), i.e.
+              // t = sign(a_jj - a_ii) 2|a_ij| / (|a_jj - a_ii| + sqrt((a_jj - a_ii)^2 + 4|a_ij|^2)),
+              // evaluated after an exact power-of-two scaling of both terms into [1, 4)
+              const float num = (sj - si) * (sj + si) + (cj - ci);
+              const float mxv = fmaxf(fabsf(num), 2.0f * beta);
+              const float sc = __int_as_float(0x7f000000 - (__float_as_int(mxv) & 0x7f800000));
+              const float nu = num * sc, b2 = 2.0f * beta * sc;
+              const float den = fabsf(nu) + sqrtf(fmaf(nu, nu, b2 * b2));
+              const float t = copysignf(__fdividef(b2, den), num);
+              const float c = rsqrtf(fmaf(t, t, 1.0f));
+              const float s_ = t * c;
+              rp = make_float4(c, e * s_, -e * s_, -__fdividef(s_ * s_, 1.0f + c));
+              dci = -t * beta;  // a_ii' = a_ii - t |a_ij|, a_jj' = a_jj + t |a_ij|
+              dcj = t * beta;
+            } else {
+              // hyperbolic: coth(2 phi) = -(a_ii + a_jj) / (2 |a_ij|), i.e.
+              // t = -2|a_ij| / (a_ii + a_jj + sqrt((a_ii + a_jj - 2|a_ij|)(a_ii + a_jj + 2|a_ij|))),
+              // with the |tanh| < 1 guard of Sec. 3.2
+              const float apd = aii + ajj;
+              const float sc = __int_as_float(0x7f000000 - (__float_as_int(apd) & 0x7f800000));
+              const float ap = apd * sc, b2 = 2.0f * beta * sc;
+              const float r2 = (ap - b2) * (ap + b2);
+              float t = (r2 > 0.0f) ? -__fdividef(b2, ap + sqrtf(r2)) : -1.0f;
+              if (!(fabsf(t) < 1.0f) || !((1.0f - t) * (1.0f + t) > 0.0f)) t = copysignf(0.9f, t);
+              const float ch = rsqrtf((1.0f - t) * (1.0f + t));
+              const float sh = t * ch;
+              rp = make_float4(ch, e * sh, e * sh, __fdividef(sh * sh, 1.0f + ch));
+              dci = t * beta;  // both diagonals move by t |a_ij| (the J-trace is invariant)
+              dcj = t * beta;
             }
+            sm.cn[bi] = ci + dci;
+            sm.cn[bj] = cj + dcj;
           }
-          sm.rotp[lane] = rp;
-          sm.rflag[lane] = rot;
         }
+        sm.rotp[lane] = rp;
+        sm.rflag[lane] = rot;
       }
       __syncthreads();
       // ---- C
@@ -451,47 +459,56 @@ __global__ void __launch_bounds__(PV_THREADS, 1)
         const float4 rp = sm.rotp[warp];
         const float q11 = rp.x, q12 = rp.y, q21 = rp.z, cm1 = rp.w;
         const float si = sm.dd[i], sj = sm.dd[j];
-        const float2 Q11 = make_float2(q11, q11), Q12 = make_float2(q12, q12), Q21 = make_float2(q21, q21);
-        float2 nfi = fma2(Q11, fi, mul2(Q21, fj));
-        float2 nfj = fma2(Q11, fj, mul2(Q12, fi));
+        Slice<R> nfi, nfj;
+#pragma unroll
+        for (int u = 0; u < R; ++u) {
+          nfi.v[u] = fmaf(q11, fi.v[u], q21 * fj.v[u]);
+          nfj.v[u] = fmaf(q11, fj.v[u], q12 * fi.v[u]);
+        }
         // + Dp (Q - I): column i gets si (q11-1) at row i and sj q21 at row j; column j
         // gets si q12 at row i and sj (q22-1) at row j
-        if (lane == (i >> 1)) {
-          if (i & 1) { nfi.y += si * cm1; nfj.y += si * q12; } else { nfi.x += si * cm1; nfj.x += si * q12; }
+        if (lane == i / R) {
+          nfi.v[i % R] += si * cm1;
+          nfj.v[i % R] += si * q12;
         }
-        if (lane == (j >> 1)) {
-          if (j & 1) { nfi.y += sj * q21; nfj.y += sj * cm1; } else { nfi.x += sj * q21; nfj.x += sj * cm1; }
+        if (lane == j / R) {
+          nfi.v[j % R] += sj * q21;
+          nfj.v[j % R] += sj * cm1;
         }
-        F2[i * (PV_LDF / 2) + lane] = nfi;
-        F2[j * (PV_LDF / 2) + lane] = nfj;
-        const float2 wi = W2[i * (PV_LDF / 2) + lane], wj = W2[j * (PV_LDF / 2) + lane];
-        float2 nwi = fma2(Q11, wi, mul2(Q21, wj));
-        float2 nwj = fma2(Q11, wj, mul2(Q12, wi));
-        if (lane == (i >> 1)) {
-          if (i & 1) { nwi.y += cm1; nwj.y += q12; } else { nwi.x += cm1; nwj.x += q12; }
+        store_slice<R>(sm.F + i * LDF, lane, nfi);
+        store_slice<R>(sm.F + j * LDF, lane, nfj);
+        const Slice<R> wi = load_slice<R>(sm.W + i * LDF, lane), wj = load_slice<R>(sm.W + j * LDF, lane);
+        Slice<R> nwi, nwj;
+#pragma unroll
+        for (int u = 0; u < R; ++u) {
+          nwi.v[u] = fmaf(q11, wi.v[u], q21 * wj.v[u]);
+          nwj.v[u] = fmaf(q11, wj.v[u], q12 * wi.v[u]);
         }
-        if (lane == (j >> 1)) {
-          if (j & 1) { nwi.y += q21; nwj.y += cm1; } else { nwi.x += q21; nwj.x += cm1; }
+        if (lane == i / R) {
+          nwi.v[i % R] += cm1;
+          nwj.v[i % R] += q12;
         }
-        W2[i * (PV_LDF / 2) + lane] = nwi;
-        W2[j * (PV_LDF / 2) + lane] = nwj;
+        if (lane == j / R) {
+          nwi.v[j % R] += q21;
+          nwj.v[j % R] += cm1;
+        }
+        store_slice<R>(sm.W + i * LDF, lane, nwi);
+        store_slice<R>(sm.W + j * LDF, lane, nwj);
       }
       __syncthreads();
     }
-    int tot = 0;
-    float dmax = 0.0f;
     if (warp == 0) {
-      tot = warp_sum_i(my_rot);
+      const int tot_w = warp_sum_i(my_rot);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) my_max = fmaxf(my_max, __shfl_xor_sync(0xffffffffu, my_max, o));
       if (lane == 0) {
-        sm.red_i[0][1] = tot;
+        sm.red_i[0][1] = tot_w;
         sm.red_f[0][2] = my_max;
       }
     }
     __syncthreads();
-    tot = sm.red_i[0][1];
-    dmax = sm.red_f[0][2];
+    const int tot = sm.red_i[0][1];
+    const float dmax = sm.red_f[0][2];
     __syncthreads();
     total_rot += tot;
     // done when nothing was rotated, or when every rotated pair was already so small that the
@@ -503,17 +520,19 @@ __global__ void __launch_bounds__(PV_THREADS, 1)
 
   // ---- 4. V = I + Wd (physical coordinates), J-orthogonalized in FP64 if requested ----------
   float wm = 0.0f;
-  for (int e = tid; e < KP * KP; e += PV_THREADS) {
+  for (int e = tid; e < KP * KP; e += NT) {
     const int r = e % KP, c = e / KP;
-    const float w = (r < k && c < k) ? sm.W[c * PV_LDF + r] : 0.0f;
+    const float w = (r < k && c < k) ? sm.W[c * LDF + r] : 0.0f;
     const double v = (double)w + ((r == c && r < k) ? 1.0 : 0.0);
-    Vs[c * PV_LDV + r] = v;
-    sm.Vf[c * PV_LDS + r] = (float)v;
+    Vs[c * LDV + r] = v;
+    sm.Vf[c * LDS + r] = (float)v;
     wm = fmaxf(wm, fabsf(w));
   }
   int ns = 0;
+  bool ns_ok = true;
   if (pp.ns_mode) {
-    wm = block_max_f(wm, sm, 3);  // includes the barrier after the V build
+    ns_ok = false;
+    wm = block_max_f<KM>(wm, sm, 3);  // includes the barrier after the V build
     const bool small_w = wm <= 9.5367431640625e-7f;  // 2^-20
     for (int it = 0; it < 3; ++it) {
       // residual M = V^T J V - J, J = diag(jphys) on rows and columns
@@ -522,35 +541,34 @@ __global__ void __launch_bounds__(PV_THREADS, 1)
         // V = I + Wd: M = Wd^T J + J Wd + Wd^T J Wd.  The linear part is exact in FP32 when it
         // cancels (Sterbenz) and rounds relative to itself otherwise; the quadratic part is at
         // most k 2^-40 and carries FP32 relative error.  Stored as fp32(J M) directly.
-        for (int e = tid; e < KP * KP; e += PV_THREADS) {
+        for (int e = tid; e < KP * KP; e += NT) {
           const int x = e % KP, j = e / KP;
           float mv = 0.0f;
           if (x < k && j < k) {
             const float jx = (float)sm.jphys[x], jj = (float)sm.jphys[j];
             float quad = 0.0f;
-            for (int r = 0; r < k; ++r)
-              quad = fmaf(sm.W[x * PV_LDF + r] * (float)sm.jphys[r], sm.W[j * PV_LDF + r], quad);
-            mv = (sm.W[x * PV_LDF + j] * jj + jx * sm.W[j * PV_LDF + x]) + quad;
+            for (int r = 0; r < k; ++r) quad = fmaf(sm.W[x * LDF + r] * (float)sm.jphys[r], sm.W[j * LDF + r], quad);
+            mv = (sm.W[x * LDF + j] * jj + jx * sm.W[j * LDF + x]) + quad;
           }
           mloc = fmaxf(mloc, fabsf(mv));
-          sm.S[j * PV_LDS + x] = (x < k) ? (float)sm.jphys[x] * mv : 0.0f;  // (J M)[x][j]
+          sm.S[j * LDS + x] = (x < k) ? (float)sm.jphys[x] * mv : 0.0f;  // (J M)[x][j]
         }
       } else {
         // FP64 mma, upper tiles (8 tj + 7 >= 16 ti) and the mirror of the strict lower part
         const int g = lane >> 2, t = lane & 3;
         const int ntj = KP / 8, ntiles = (KP / 16) * ntj;
-        for (int tile = warp; tile < ntiles; tile += PV_WARPS) {
+        for (int tile = warp; tile < ntiles; tile += NW) {
           const int ti = tile / ntj, tj = tile % ntj;
           if (8 * tj + 7 < 16 * ti) continue;
           double c4[4] = {0.0, 0.0, 0.0, 0.0};
           for (int kq = 0; kq < KP; kq += 16) {
             double av[8], bv[4];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) av[u] = Vs[(16 * ti + g + 8 * (u & 1)) * PV_LDV + kq + 4 * t + (u >> 1)];
+            for (int u = 0; u < 8; ++u) av[u] = Vs[(16 * ti + g + 8 * (u & 1)) * LDV + kq + 4 * t + (u >> 1)];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
               const int r = kq + 4 * t + u;
-              const double v = Vs[(8 * tj + g) * PV_LDV + r];
+              const double v = Vs[(8 * tj + g) * LDV + r];
               bv[u] = (r < k && sm.jphys[r] < 0) ? -v : v;
             }
             dmma16816(c4, av, bv);
@@ -558,36 +576,43 @@ __global__ void __launch_bounds__(PV_THREADS, 1)
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
             const int i = 16 * ti + g + 8 * (u >> 1), j = 8 * tj + 2 * t + (u & 1);
+            if (j < i) continue;  // written once, from the tile holding (j, i) ... (i, j), j >= i
             double v = c4[u];
             if (i == j && i < k) v -= (sm.jphys[i] < 0) ? -1.0 : 1.0;
-            sm.M[j * PV_LDV + i] = v;
-            sm.M[i * PV_LDV + j] = v;
+            sm.M[j * LDV + i] = v;
+            sm.M[i * LDV + j] = v;
           }
         }
         __syncthreads();
-        for (int e = tid; e < KP * KP; e += PV_THREADS) {
+        for (int e = tid; e < KP * KP; e += NT) {
           const int x = e % KP, j = e / KP;
-          const double mv = sm.M[j * PV_LDV + x];
+          const double mv = sm.M[j * LDV + x];
           mloc = fmaxf(mloc, (float)fabs(mv));
-          sm.S[j * PV_LDS + x] = (x < k) ? (float)((sm.jphys[x] < 0) ? -mv : mv) : 0.0f;
+          sm.S[j * LDS + x] = (x < k) ? (float)((sm.jphys[x] < 0) ? -mv : mv) : 0.0f;
         }
       }
-      const float mm = block_max_f(mloc, sm, 0);
-      if (mm <= 4.0e-16f) break;
+      const float mm = block_max_f<KM>(mloc, sm, 0);
+      if (mm <= 4.0e-16f) {
+        ns_ok = true;
+        break;
+      }
       // V <- V - V (J M) / 2: the correction is O(|M|), formed in FP32 from the FP32 copy of V
-      for (int e = tid; e < KP * KP; e += PV_THREADS) {
+      for (int e = tid; e < KP * KP; e += NT) {
         const int r = e % KP, j = e / KP;
-        float s = 0.0f;
-        for (int x = 0; x < k; ++x) s = fmaf(sm.Vf[x * PV_LDS + r], sm.S[j * PV_LDS + x], s);
-        Vs[j * PV_LDV + r] -= 0.5 * (double)s;
+        float sum = 0.0f;
+        for (int x = 0; x < k; ++x) sum = fmaf(sm.Vf[x * LDS + r], sm.S[j * LDS + x], sum);
+        Vs[j * LDV + r] -= 0.5 * (double)sum;
       }
       ++ns;
       __syncthreads();
       // predicted residual after this step: quadratic term + FP32 rounding of the correction
-      if (mm * mm + 1.0e-6f * mm <= 2.0e-16f) break;
-      for (int e = tid; e < KP * KP; e += PV_THREADS) {
+      if (mm * mm + 1.0e-6f * mm <= 2.0e-16f) {
+        ns_ok = true;
+        break;
+      }
+      for (int e = tid; e < KP * KP; e += NT) {
         const int r = e % KP, c = e / KP;
-        sm.Vf[c * PV_LDS + r] = (float)Vs[c * PV_LDV + r];
+        sm.Vf[c * LDS + r] = (float)Vs[c * LDV + r];
       }
       __syncthreads();
     }
@@ -595,20 +620,34 @@ __global__ void __launch_bounds__(PV_THREADS, 1)
     __syncthreads();
   }
   const long long t_ns = clock64();
+  if (!ns_ok) {  // V is not J-unitary to FP64 accuracy after the step budget: FP64 pivot kernel
+    if (tid == 0) {
+      a.skip[pair] = 2;
+      st.rotations = total_rot;
+      st.inner_sweeps = inner + 1;
+      st.ns_steps = ns;
+      st.cyc[0] = t_stats - t_start;
+      st.cyc[1] = t_chol - t_stats;
+      st.cyc[2] = t_inner - t_chol;
+      st.cyc[3] = t_ns - t_inner;
+      stats[pair] = st;
+    }
+    return;
+  }
   // V_P = P V Pi: V_P[perm[r]][l] = V[r][lpos[l]]
-  double* out = vp + (size_t)pair * JAC_KMAX * JAC_KMAX;
-  for (int e = tid; e < KP * KP; e += PV_THREADS) {
+  double* out = a.vp + (size_t)pair * a.apld * a.apld;
+  for (int e = tid; e < KP * KP; e += NT) {
     const int r = e % KP, l = e / KP;
     double v = 0.0;
     int row = r;
     if (r < k && l < k) {
-      v = Vs[sm.lpos[l] * PV_LDV + r];
+      v = Vs[sm.lpos[l] * LDV + r];
       row = sm.perm[r];
     }
-    out[l * JAC_KMAX + row] = v;
+    out[l * a.apld + row] = v;
   }
   if (tid == 0) {
-    skip[pair] = 0;
+    a.skip[pair] = 0;
     st.rotations = total_rot;
     st.inner_sweeps = inner + 1;
     st.ns_steps = ns;
@@ -620,6 +659,24 @@ __global__ void __launch_bounds__(PV_THREADS, 1)
   }
 }
 
-size_t pivot_smem_bytes() { return sizeof(PivotSmem); }
+size_t pivot_smem_bytes(int km) { return km == 32 ? sizeof(PivotSmem<32>) : sizeof(PivotSmem<64>); }
+
+// Host side of the two instantiations (a kernel template is launched from its own translation unit).
+int pivot_set_attributes() {
+  bool ok = cudaFuncSetAttribute(k_pivot<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(PivotSmem<32>)) == cudaSuccess;
+  ok &= cudaFuncSetAttribute(k_pivot<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PivotSmem<64>)) ==
+        cudaSuccess;
+  return ok ? 0 : 1;
+}
+
+// Grid (max_half, nprob): one CTA of km*16 threads per pivot block.
+void pivot_launch(int km, int max_half, int nprob, cudaStream_t st, const JacProb* probs, int s,
+                  const PivotParams& pp) {
+  if (km == 32)
+    k_pivot<32><<<dim3(max_half, nprob), 32 * 16, sizeof(PivotSmem<32>), st>>>(probs, s, pp);
+  else
+    k_pivot<64><<<dim3(max_half, nprob), 64 * 16, sizeof(PivotSmem<64>), st>>>(probs, s, pp);
+}
 
 }  // namespace jac

@@ -1,0 +1,143 @@
+"""Batched entry point (jacobi_eig_batched) vs the CPU oracle, problem by problem.
+
+The inputs follow the batched workload (orders uniform in [8, 128], Gaussian G, a random 30% of
+the signs -1), in small batches the oracle finishes in seconds; every problem of a batch is held
+to the single-solve tolerances (FP64) or to the same bounds at eps = 2^-24 (FP32-only sweeps).
+"""
+import numpy as np
+import pytest
+
+from checks import EPS32, compare, to_np
+
+pytestmark = pytest.mark.gpu
+
+
+def run_batched(Gs, Js, dev, want_u=True, raise_on_error=False, **kw):
+    import torch
+
+    from paper_1008_0201_gb300 import binding
+
+    opts = binding.default_opts(**kw)
+    Gd = [torch.from_numpy(np.ascontiguousarray(G)).to(dev) for G in Gs]
+    Jd = None if Js is None else [None if J is None else torch.from_numpy(J).to(dev) for J in Js]
+    outs, rc = binding.jacobi_eig_batched(Gd, Jd, opts, want_u=want_u, raise_on_error=raise_on_error)
+    torch.cuda.synchronize()
+    return [to_np(o) for o in outs], rc
+
+
+def small_batch(count, salt, lo=8, hi=128, pd_every=0):
+    from paper_1008_0201_gb300 import inputs
+
+    Gs, Js = inputs.config4_batched(count=count, lo=lo, hi=hi, salt=salt)
+    if pd_every:
+        Js = [None if i % pd_every == 0 else J for i, J in enumerate(Js)]
+    return Gs, Js
+
+
+def check_all(Gs, Js, outs, eps=None):
+    for i, (G, J, o) in enumerate(zip(Gs, Js, outs)):
+        assert o["info"]["status"] == 0, (i, G.shape, o["info"])
+        Jf = np.ones(G.shape[1], dtype=np.int8) if J is None else J
+        if eps is None:
+            compare(G, Jf, o)
+        else:
+            compare(G, Jf, o, eps=eps)
+
+
+@pytest.mark.parametrize("ordering", ["round_robin", "modulus", "modulus_mod"])
+def test_batched_fp64_uneven_orders(cuda_dev, ordering):
+    Gs, Js = small_batch(20, salt=11, pd_every=4)
+    outs, rc = run_batched(Gs, Js, cuda_dev, ordering=ordering)
+    assert rc == 0
+    check_all(Gs, Js, outs)
+
+
+@pytest.mark.parametrize("factor", ["chol", "chol_signpiv"])
+def test_batched_fp32_only(cuda_dev, factor):
+    Gs, Js = small_batch(20, salt=12, pd_every=5)
+    outs, rc = run_batched(Gs, Js, cuda_dev, precision="fp32_only", factor=factor)
+    assert rc == 0
+    check_all(Gs, Js, outs, eps=EPS32)
+
+
+def test_batched_size_class_edges(cuda_dev):
+    """Orders at the class boundaries (one pivot block up to 64 columns, 32-wide blocks above),
+    tall factors (m > n) and the smallest problems."""
+    g = np.random.default_rng(77)
+    shapes = [(8, 8), (9, 2), (31, 31), (32, 32), (33, 33), (40, 33), (64, 64), (65, 65), (96, 97 - 1),
+              (128, 128), (130, 127), (5, 3), (2, 2), (70, 1)]
+    Gs, Js = [], []
+    for i, (m, n) in enumerate(shapes):
+        Gs.append(g.standard_normal((m, n)))
+        J = np.ones(n, dtype=np.int8)
+        J[g.choice(n, size=int(round(0.3 * n)), replace=False)] = -1
+        Js.append(J if i % 3 else None)
+    outs, rc = run_batched(Gs, Js, cuda_dev)
+    assert rc == 0
+    check_all(Gs, Js, outs)
+    # a single column needs no sweep
+    assert outs[-1]["info"]["sweeps"] == 0
+
+
+def test_batched_composition_independent(cuda_dev):
+    """A problem's result does not depend on the rest of the batch (bit for bit), nor on
+    repetition."""
+    Gs, Js = small_batch(12, salt=13)
+    full, rc = run_batched(Gs, Js, cuda_dev)
+    assert rc == 0
+    again, _ = run_batched(Gs, Js, cuda_dev)
+    for a, b in zip(full, again):
+        assert np.array_equal(a["lam"], b["lam"]) and np.array_equal(a["V"], b["V"])
+    for i in (0, 5, 11):
+        alone, rc1 = run_batched([Gs[i]], [Js[i]], cuda_dev)
+        assert rc1 == 0
+        assert np.array_equal(alone[0]["lam"], full[i]["lam"])
+        assert np.array_equal(alone[0]["G"], full[i]["G"])
+        assert np.array_equal(alone[0]["V"], full[i]["V"])
+
+
+def test_batched_failures_are_per_problem(cuda_dev):
+    """A non-finite input, a sign other than +-1 and a rank-deficient indefinite factor fail
+    their own problem only; the other problems are solved to the usual tolerances."""
+    from paper_1008_0201_gb300 import binding
+
+    g = np.random.default_rng(91)
+    Gs = [g.standard_normal((n, n)) for n in (20, 24, 40, 16, 70)]
+    Js = [np.where(g.random(G.shape[1]) < 0.3, -1, 1).astype(np.int8) for G in Gs]
+    Gs[1][3, 5] = np.inf                       # non-finite
+    Js[2] = Js[2].copy()
+    Js[2][4] = 0                               # invalid sign
+    Gs[3][:, 7] = Gs[3][:, 2]                  # duplicate column in one pivot block: A_P singular
+    Js[3][2], Js[3][7] = 1, -1
+    G1_before = Gs[1].copy()
+    outs, rc = run_batched(Gs, Js, cuda_dev)
+    st = [o["info"]["status"] for o in outs]
+    assert st[1] == binding.JAC_ENONFINITE
+    assert st[2] == -7
+    assert st[3] == binding.JAC_ENOTPD
+    assert rc == binding.JAC_ENONFINITE        # first failing problem in input order
+    for i in (0, 4):
+        assert st[i] == 0
+        compare(Gs[i], Js[i], outs[i])
+    # a problem that failed validation keeps its input
+    assert np.array_equal(np.nan_to_num(outs[1]["G"], posinf=1e300), np.nan_to_num(G1_before, posinf=1e300))
+
+
+def test_batched_argument_errors(cuda_dev):
+    import torch
+
+    from paper_1008_0201_gb300 import binding
+
+    G = torch.randn(20, 20, dtype=torch.float64, device=cuda_dev)
+    with pytest.raises(binding.JacobiError) as e:
+        binding.jacobi_eig_batched([G], None, binding.default_opts(ordering="cycle_weight"))
+    assert e.value.code == -8
+    with pytest.raises(binding.JacobiError) as e:
+        binding.jacobi_eig_batched([G], None, binding.default_opts(precision="fp32"))
+    assert e.value.code == -8
+    big = torch.randn(140, 129, dtype=torch.float64, device=cuda_dev)
+    with pytest.raises(binding.JacobiError) as e:
+        binding.jacobi_eig_batched([G, big], None, binding.default_opts())
+    assert e.value.code == -3
+    outs, rc = binding.jacobi_eig_batched([], None, binding.default_opts())
+    assert outs == [] and rc == 0

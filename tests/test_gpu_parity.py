@@ -116,6 +116,25 @@ def test_already_diagonal(cuda_dev):
     assert np.array_equal(out["lam"], np.array([-36.0, -16.0, -4.0, 1.0, 9.0, 25.0]))
 
 
+@pytest.mark.parametrize("signs", ["same", "opposite"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_ill_conditioned_block(cuda_dev, signs, precision):
+    """Two nearly parallel columns (angle ~1e-4, kappa(A~) ~ 1e8) inside one pivot block: the
+    FP32 Cholesky of the scaled Gram breaks down there, the block is factored and rotated in
+    FP64 instead, and the result still meets the oracle tolerances."""
+    g = np.random.default_rng(4242)
+    m, n = 80, 40
+    G = g.standard_normal((m, n))
+    G[:, 7] = G[:, 2] + 1e-4 * g.standard_normal(m)
+    J = np.ones(n, dtype=np.int8)
+    J[g.choice(n, size=12, replace=False)] = -1
+    J[2] = 1
+    J[7] = 1 if signs == "same" else -1
+    out = run(G, J, cuda_dev, block_w=20, precision=precision)
+    assert out["status"] == 0, out["info"]
+    compare(G, J, out)
+
+
 def test_deterministic(cuda_dev):
     from paper_1008_0201_gb300 import inputs
 
