@@ -42,7 +42,10 @@
  * closed-form 2x2 eigenvalues, prescribed spectra Q diag(sigma) W, exact characteristic
  * polynomial roots for n <= 6, SVD for J = I, and the invariants V^* J V = J, G0 V = G,
  * G^* G diagonal.  The block orderings (modulus, modified modulus, round-robin, per-cycle
- * weight) are pinned by exhaustive enumeration.
+ * weight) are pinned by exhaustive enumeration.  The eigendecomposition adjoint
+ * (oracle_eig_backward, no counterpart in the paper) is pinned by the Hellmann-Feynman
+ * eigenvalue derivatives, the closed form on diagonal H and central finite differences of a
+ * loss on eigenvalues and eigenvectors with LAPACK as the forward map.
  *
  * Precision: IEEE double throughout the method; the check routines accumulate in long double
  * (80-bit on x86-64, binary128 on aarch64).  Compile with -ffp-contract=off so that results
@@ -62,7 +65,8 @@
  * 2: hyperbolic pairs rotated with the trigonometric formula.
  * 3: complex phase not conjugated in g_i'.
  * 4: eigenvalue sign j_k dropped.
- * 5: V accumulation skipped on the second column of each pair.                          */
+ * 5: V accumulation skipped on the second column of each pair.
+ * 6: adjoint formed with (U_bar^T U) in place of (U^T U_bar).                            */
 static int g_mutation = 0;
 void oracle_set_mutation(int k) { g_mutation = k; }
 int oracle_get_mutation(void) { return g_mutation; }
@@ -568,7 +572,9 @@ void oracle_eig_backward(int n, const double* lambda, const double* U, const dou
         wide gap = (wide)lambda[j] - (wide)lambda[i];
         if (fabsl(gap) > (wide)mask * lmax) {
           wide s = 0;
-          for (int r = 0; r < n; ++r) s += (wide)U[(size_t)i * n + r] * U_bar[(size_t)j * n + r];
+          for (int r = 0; r < n; ++r)
+            s += (g_mutation == 6) ? (wide)U_bar[(size_t)i * n + r] * U[(size_t)j * n + r]
+                                   : (wide)U[(size_t)i * n + r] * U_bar[(size_t)j * n + r];
           v = s / gap;
         }
       }
