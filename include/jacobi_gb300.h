@@ -164,9 +164,9 @@ int jacobi_eig_pd(int m, int n, int dtype, void* G, int ldg, const jac_opts* opt
  * nothing.  Problem b is jacobi_hsvd(m[b], n[b], dtype, G[b], ldg[b], J[b], opts, lambda[b],
  * U[b], ldu[b], V[b], ldv[b], &info[b]) except that opts->block_w is ignored: the block width
  * is chosen per size class (one pivot block of the whole problem for n <= 64, blocks of 32
- * columns above).
+ * columns above).  Batches above 32768 problems run as consecutive chunks of that size.
  *  1 batch         >= 0 problems (0: nothing is done).
- *  2 m, 3 n        host int[batch]; 1 <= n[b] <= m[b], n[b] <= 128 in this version.
+ *  2 m, 3 n        host int[batch]; 1 <= n[b] <= m[b], n[b] <= 20000.
  *  4 dtype         JAC_R64.
  *  5 G, 6 ldg      host arrays of device pointers / leading dimensions, as jacobi_hsvd.
  *  7 J             host array of device int8 pointers; NULL (the array) means J = I for every
@@ -189,6 +189,39 @@ int jacobi_eig_batched(int batch, const int* m, const int* n, int dtype, void* c
                        const int* ldg, const int8_t* const* J, const jac_opts* opts,
                        double* const* lambda, void* const* U, const int* ldu, void* const* V,
                        const int* ldv, jac_info* info, jac_stream_t stream);
+
+/*
+ * jacobi_eig_backward -- adjoint of the eigendecomposition returned by jacobi_hsvd /
+ * jacobi_eig_pd / jacobi_eig_batched for square problems (m = n).  The paper computes the
+ * forward map only; this is the standard adjoint of the symmetric eigendecomposition
+ * H = G J G^T = U diag(lambda) U^T (U orthonormal, Sec. 3.2: u_k = g_k/||g_k||):
+ *     H_bar = U sym(diag(lambda_bar) + F o (U^T U_bar)) U^T,  sym(X) = (X + X^T)/2,
+ *     F_ij = 1/(lambda_j - lambda_i) for i != j, F_ii = 0, and F_ij = 0 where
+ *     |lambda_i - lambda_j| <= deg_tol max_k |lambda_k| (exact only for losses invariant inside
+ *     a degenerate eigenspace);
+ * and, through the factor, G_bar = (H_bar + H_bar^T) G J = 2 H_bar G J.
+ * A batch of problems of one order n at fixed element strides; all arrays device, column-major.
+ *  1 batch          0 <= batch <= 65535
+ *  2 n              order, 1 <= n <= 20000
+ *  3 lambda, 4 s_lam            eigenvalues (as returned, ascending), problem b at lambda + b s_lam
+ *  5 U, 6 ldu, 7 s_u            orthonormal eigenvectors, n x n
+ *  8 lambda_bar, 9 s_lbar       dL/dlambda, or NULL (zero)
+ * 10 U_bar, 11 ldub, 12 s_ubar  dL/dU, or NULL (zero)
+ * 13 deg_tol        >= 0 (1e-12 is a sensible default)
+ * 14 H_bar, 15 ldh, 16 s_h      output dL/dH, n x n, exactly symmetric
+ * 17 G, 18 ldg, 19 s_g          the input factor (G_in, not the overwritten one), or NULL
+ * 20 J, 21 s_j                  int8 signs of G's columns, or NULL (J = I)
+ * 22 G_bar, 23 ldgb, 24 s_gb    output dL/dG, or NULL (then G may be NULL)
+ * 25 stream
+ * Returns 0, a negative argument position, JAC_ENOMEM or JAC_ECUDA.  Asynchronous on stream
+ * (its n x n x batch scratch comes from cudaMallocAsync on that stream).
+ */
+int jacobi_eig_backward(int batch, int n, const double* lambda, long long s_lam, const double* U,
+                        int ldu, long long s_u, const double* lambda_bar, long long s_lbar,
+                        const double* U_bar, int ldub, long long s_ubar, double deg_tol,
+                        double* H_bar, int ldh, long long s_h, const double* G, int ldg,
+                        long long s_g, const int8_t* J, long long s_j, double* G_bar, int ldgb,
+                        long long s_gb, jac_stream_t stream);
 
 /*
  * jacobi_sched_pairs -- the device scheduler on its own (Sec. 2.4), for inspection and tests.

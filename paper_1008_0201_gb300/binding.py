@@ -53,7 +53,7 @@ _lib = None
 
 EXPORTS = ("jacobi_default_opts", "jacobi_status_string", "jacobi_version", "jacobi_hsvd", "jacobi_eig_pd",
            "jacobi_sched_pairs", "jacobi_profile_begin", "jacobi_profile_read", "jacobi_profile_end",
-           "jacobi_sched_pairs_noalloc", "jacobi_eig_batched")
+           "jacobi_sched_pairs_noalloc", "jacobi_eig_batched", "jacobi_eig_backward")
 KERNEL = {"gram": 0, "pivot": 1, "update": 2}
 
 
@@ -81,6 +81,9 @@ def load_library(path=LIB_PATH):
     lib.jacobi_sched_pairs.restype = I
     lib.jacobi_eig_batched.argtypes = [I, P, P, I, P, P, P, ctypes.POINTER(JacOpts), P, P, P, P, P, P, P]
     lib.jacobi_eig_batched.restype = I
+    L = ctypes.c_longlong
+    lib.jacobi_eig_backward.argtypes = [I, I, P, L, P, I, L, P, L, P, I, L, D, P, I, L, P, I, L, P, L, P, I, L, P]
+    lib.jacobi_eig_backward.restype = I
     lib.jacobi_sched_pairs_noalloc.argtypes = [I, I, P, P, P, I, ctypes.POINTER(ctypes.c_int), P]
     lib.jacobi_sched_pairs_noalloc.restype = I
     lib.jacobi_profile_begin.argtypes = [I]
@@ -254,6 +257,81 @@ def jacobi_eig_batched(Gs, Js=None, opts=None, want_u=False, raise_on_error=True
         outs.append(dict(lam=lams[i], G=Gts[i].t(), U=Uts[i].t() if Uts is not None else None,
                          V=Vts[i].t() if Vts is not None else None, info=infos[i].as_dict()))
     return outs, rc
+
+
+def jacobi_eig_batched_uniform(G, J=None, opts=None, want_u=True, raise_on_error=True):
+    """Batched solve of a stack of equal-shape problems.  G: (batch, m, n) CUDA tensor, J: None
+    (J = I) or (batch, n) signs.  Outputs are written straight into stacked tensors:
+    returns dict(lam (batch, n), G (batch, m, n) = G_in V, U (batch, m, n) or None,
+    V (batch, n, n) or None, infos, status)."""
+    import numpy as np
+
+    if opts is None:
+        opts = default_opts()
+    _check_cuda(G, "G")
+    batch, m, n = G.shape
+    dev = G.device
+    Gt = G.to(torch.float64).transpose(-1, -2).contiguous()  # (batch, n, m): column-major m x n each
+    lam = torch.empty((batch, n), dtype=torch.float64, device=dev)
+    Ut = torch.empty((batch, n, m), dtype=torch.float64, device=dev) if want_u else None
+    Vt = torch.empty((batch, n, n), dtype=torch.float64, device=dev) if opts.want_v else None
+    Jd = None
+    if J is not None:
+        _check_cuda(J, "J")
+        Jd = J.to(device=dev, dtype=torch.int8).reshape(batch, n).contiguous()
+    idx = np.arange(batch, dtype=np.uint64)
+    ptrs = lambda t, per: (np.uint64(t.data_ptr()) + idx * np.uint64(per)).astype(np.uint64)
+    ms = np.full(batch, m, dtype=np.int32)
+    ns = np.full(batch, n, dtype=np.int32)
+    rc, infos = jacobi_eig_batched_raw(
+        ms, ns, ptrs(Gt, 8 * m * n), ms, ptrs(Jd, n) if Jd is not None else None, opts, ptrs(lam, 8 * n),
+        ptrs(Ut, 8 * m * n) if Ut is not None else None, ms if Ut is not None else None,
+        ptrs(Vt, 8 * n * n) if Vt is not None else None, ns if Vt is not None else None, _stream(dev).value or 0)
+    if rc < 0 or rc in (JAC_ECUDA, JAC_ENOMEM) or (rc != JAC_OK and raise_on_error):
+        raise JacobiError(rc, status_string(rc))
+    return dict(lam=lam, G=Gt.transpose(-1, -2), U=Ut.transpose(-1, -2) if Ut is not None else None,
+                V=Vt.transpose(-1, -2) if Vt is not None else None, infos=infos, status=rc)
+
+
+def jacobi_eig_backward(lam, U, lam_bar=None, U_bar=None, deg_tol=1e-12, G=None, J=None):
+    """Adjoint of the eigendecomposition of square problems.  lam (batch, n), U (batch, n, n)
+    (or unbatched (n,), (n, n)); lam_bar / U_bar like them or None.  With G (the input factor,
+    same shape as U) and J ((batch, n) signs or None) also returns G_bar = 2 H_bar G J.
+    Returns (H_bar, G_bar or None), shaped like U."""
+    lib = load_library()
+    _check_cuda(U, "U")
+    unbatched = U.dim() == 2
+    if unbatched:
+        lam, U = lam.unsqueeze(0), U.unsqueeze(0)
+        lam_bar = lam_bar.unsqueeze(0) if lam_bar is not None else None
+        U_bar = U_bar.unsqueeze(0) if U_bar is not None else None
+        G = G.unsqueeze(0) if G is not None else None
+        J = J.unsqueeze(0) if J is not None else None
+    batch, n, n2 = U.shape
+    if n2 != n:
+        raise ValueError("U must be square (m = n)")
+    dev = U.device
+    cm = lambda X: X.to(torch.float64).transpose(-1, -2).contiguous()  # column-major storage
+    lamc = lam.to(torch.float64).contiguous()
+    Uc = cm(U)
+    lbc = lam_bar.to(device=dev, dtype=torch.float64).contiguous() if lam_bar is not None else None
+    Ubc = cm(U_bar.to(dev)) if U_bar is not None else None
+    Gc = cm(G.to(dev)) if G is not None else None
+    Jc = J.to(device=dev, dtype=torch.int8).reshape(batch, n).contiguous() if J is not None else None
+    Hb = torch.empty((batch, n, n), dtype=torch.float64, device=dev)
+    Gb = torch.empty((batch, n, n), dtype=torch.float64, device=dev) if G is not None else None
+    vp = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None
+    nn = n * n
+    rc = lib.jacobi_eig_backward(batch, n, vp(lamc), n, vp(Uc), n, nn, vp(lbc), n, vp(Ubc), n, nn, float(deg_tol),
+                                 vp(Hb), n, nn, vp(Gc), n, nn, vp(Jc), n, vp(Gb), n, nn, _stream(dev))
+    if rc != JAC_OK:
+        raise JacobiError(rc, status_string(rc))
+    Hb = Hb.transpose(-1, -2)
+    Gb = Gb.transpose(-1, -2) if Gb is not None else None
+    if unbatched:
+        Hb = Hb[0]
+        Gb = Gb[0] if Gb is not None else None
+    return Hb, Gb
 
 
 def jacobi_sched_pairs(nb, ordering, weights=None, device="cuda", max_steps=None, noalloc=False):

@@ -631,7 +631,7 @@ int solve_batched(int batch, const int* m, const int* n, int dtype, void* const*
   if (o.want_v && (!V || !ldv)) return !V ? -12 : -13;
   for (int b = 0; b < batch; ++b) {
     if (m[b] < 1) return -2;
-    if (n[b] < 1 || n[b] > m[b] || n[b] > 128) return -3;
+    if (n[b] < 1 || n[b] > m[b] || n[b] > 20000) return -3;
     if (!G[b]) return -5;
     if (ldg[b] < m[b]) return -6;
     if (!lambda[b]) return -9;

@@ -158,7 +158,8 @@ __global__ void __launch_bounds__(256) k_update32(const JacProb* __restrict__ pr
 //   transA = 1: op(A)[i][r] = A[i * lda + r]  (A stored K x Mr: C = A^T B)
 //   transA = 0: op(A)[i][r] = A[r * lda + i]  (A stored Mr x K)
 //   sb: optional +-1 per r (row signs of B); dsub: optional, subtracted on the diagonal.
-//   sym = 1: only tiles with tile_j >= tile_i are computed and mirrored (C symmetric).
+//   sym = 1: only tiles with tile_j >= tile_i are computed, and only entries j >= i are stored,
+//            each mirrored (C exactly symmetric; Mr == Nc).
 // Grid (ceil(Mr/32), ceil(Nc/32)); 128 threads; K chunk 32.
 #define DG_T 32
 #define DG_LD (DG_T + 2)
@@ -229,11 +230,11 @@ __global__ void __launch_bounds__(128) k_gemm64(int Mr, int Nc, int K, const dou
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int i = i0 + wi + g + 8 * (u >> 1), j = j0 + wj + 8 * h + 2 * t + (u & 1);
-      if (i < Mr && j < Nc) {
+      if (i < Mr && j < Nc && (!sym || j >= i)) {
         double v = acc[h][u];
         if (dsub && i == j) v -= (dsub[i] < 0) ? -1.0 : 1.0;
         C[(size_t)j * ldc + i] = v;
-        if (sym && bj > bi) C[(size_t)i * ldc + j] = v;
+        if (sym && j > i) C[(size_t)i * ldc + j] = v;  // exactly symmetric: (j, i) is never computed
       }
     }
 }

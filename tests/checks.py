@@ -69,7 +69,8 @@ def compare(G0, J, out, ref=None, check_vectors=True, kappa=None, eps=EPS):
             s = np.linalg.norm(u - np.dot(u, v) * v)  # sin of the angle, no 1 - cos^2 cancellation
             bound = 50 * n * eps * kappa / relgap + 1e-14
             assert s <= bound, ("eigenvector", i, s, bound)
-            worst = max(worst, s * relgap / (50 * n * eps * kappa))
+            if np.isfinite(relgap):
+                worst = max(worst, s * relgap / (50 * n * eps * kappa))
         res["vec_frac_of_bound"] = worst
     return res
 

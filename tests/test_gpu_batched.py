@@ -135,9 +135,9 @@ def test_batched_argument_errors(cuda_dev):
     with pytest.raises(binding.JacobiError) as e:
         binding.jacobi_eig_batched([G], None, binding.default_opts(precision="fp32"))
     assert e.value.code == -8
-    big = torch.randn(140, 129, dtype=torch.float64, device=cuda_dev)
+    wide = torch.randn(10, 12, dtype=torch.float64, device=cuda_dev)  # n > m
     with pytest.raises(binding.JacobiError) as e:
-        binding.jacobi_eig_batched([G, big], None, binding.default_opts())
+        binding.jacobi_eig_batched([G, wide], None, binding.default_opts())
     assert e.value.code == -3
     outs, rc = binding.jacobi_eig_batched([], None, binding.default_opts())
     assert outs == [] and rc == 0
