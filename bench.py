@@ -29,7 +29,14 @@ N = 512
 BLOCK_W = 32
 EPS = 2.0 ** -53
 METRIC = "time-to-solution and matrices/s at stated eigen rel-error; % FP64/FP32 tensor peak"
-WORKLOAD = "hyperbolic SVD 512x512 Gaussian, J=diag(+1x256,-1x256), w=32, HFSC, per-cycle weight ordering"
+WORKLOAD = "hyperbolic SVD 512x512 Gaussian, J=diag(+1x256,-1x256), w=32"
+
+
+def variant_name(args):
+    """Paper's naming (Sec. 3.2): H + F (full block) / B (block-oriented) + SC (sign-pivoted
+    Cholesky), with the block ordering."""
+    name = "H" + ("B" if args.block_mode == "oriented" else "F") + ("SC" if args.factor == "chol_signpiv" else "")
+    return "%s, %s ordering" % (name, args.ordering.replace("_", "-"))
 # dtype of the arithmetic: FP64 contractions and FP32 inner rotations; the mixed mode runs its
 # early sweeps on an FP32 copy (FP32 products) before the FP64 polish
 
@@ -40,8 +47,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--ordering", default="cycle_weight")
+    ap.add_argument("--ordering", default="round_robin")
     ap.add_argument("--factor", default="chol_signpiv")
+    ap.add_argument("--block-mode", default="oriented", choices=["full", "oriented"])
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -147,8 +155,7 @@ def reference_arm(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "matrices/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD.replace("HFSC, per-cycle weight ordering",
-                                                    "row-cyclic pointwise oracle"), "n": N},
+            "config": {"workload": WORKLOAD + ", row-cyclic pointwise oracle", "n": N},
             "cpu_baseline": {"value": val, "unit": "matrices/s", "cores": 1, "kind": "oracle",
                              "sample": "each step one full solve (%d sweeps); warm-up on 128x128" % sweeps},
             "e2e": {"value": val, "unit": "matrices/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -186,7 +193,7 @@ def main():
     G, J = inputs.config2_hyperbolic(n=N, salt=rank)
     m, n = G.shape
     opts = binding.default_opts(block_w=BLOCK_W, ordering=args.ordering, factor=args.factor,
-                                precision=args.precision)
+                                block_mode=args.block_mode, precision=args.precision)
     stream = torch.cuda.current_stream(dev)
     sptr = stream.cuda_stream
     # inputs resident in HBM: one fresh column-major copy per step (G is overwritten in place)
@@ -306,8 +313,10 @@ def main():
             "metric": METRIC, "value": world * 1000.0 / ms, "unit": "matrices/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": n, "block_w": BLOCK_W, "ordering": args.ordering,
-                       "factor": args.factor, "precision": args.precision, "sweeps": info["sweeps"],
+            "config": {"workload": WORKLOAD + ", " + variant_name(args), "n": n, "block_w": BLOCK_W,
+                       "ordering": args.ordering,
+                       "factor": args.factor, "block_mode": args.block_mode, "precision": args.precision,
+                       "sweeps": info["sweeps"],
                        "fp32_sweeps": info["lowp_sweeps"], "steps_per_sweep": info["steps_per_sweep"],
                        "pivot_phase_share": [c / max(1, sum(info["pivot_cycles"])) for c in info["pivot_cycles"]],
                        "sweep_max_scaled": ["%.2e" % v for v in info["sweep_max_scaled"]],

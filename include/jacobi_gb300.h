@@ -65,7 +65,13 @@ enum jac_ordering {
 };
 
 /* Pivot block processing (Sec. 2.2). */
-enum jac_block_mode { JAC_BLOCK_FULL = 0 /* diagonalize each pivot block (HF/HFSC, TF) */ };
+enum jac_block_mode {
+  JAC_BLOCK_FULL = 0,     /* diagonalize each pivot block (full block: HF / HFSC, Sec. 2.2) */
+  JAC_BLOCK_ORIENTED = 1  /* block-oriented (HB / HBSC, Sec. 2.2 and Algorithm 3.4): the first
+                             step of a sweep annihilates every off-diagonal element of its pivot
+                             blocks once, the other steps only the elements of the cross block
+                             A_pq, once */
+};
 
 /* Factorization of the pivot block A_P = G_P^* G_P (Sec. 3.2). */
 enum jac_factor {

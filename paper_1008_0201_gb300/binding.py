@@ -18,6 +18,7 @@ JAC_R64, JAC_C128 = 0, 1
 ORDER = {"modulus": 0, "modulus_mod": 1, "round_robin": 2, "cycle_weight": 3}
 FACTOR = {"chol": 0, "chol_signpiv": 2}
 PRECISION = {"fp64": 0, "fp32": 1, "fp32_only": 2}
+BLOCK_MODE = {"full": 0, "oriented": 1}
 
 
 class JacOpts(ctypes.Structure):
@@ -107,6 +108,8 @@ def default_opts(**kw):
             val = FACTOR[val]
         elif key == "precision" and isinstance(val, str):
             val = PRECISION[val]
+        elif key == "block_mode" and isinstance(val, str):
+            val = BLOCK_MODE[val]
         setattr(o, key, val)
     return o
 

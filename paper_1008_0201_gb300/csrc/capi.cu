@@ -156,7 +156,7 @@ int check_opts(const jac_opts& o, int argpos, bool batch) {
   if (o.block_w < 1 || o.block_w > JAC_WMAX) return -argpos;
   if (o.ordering < 0 || o.ordering > 3) return -argpos;
   if (batch && o.ordering == JAC_ORDER_CYCLE_WEIGHT) return -argpos;
-  if (o.block_mode != JAC_BLOCK_FULL) return -argpos;
+  if (o.block_mode != JAC_BLOCK_FULL && o.block_mode != JAC_BLOCK_ORIENTED) return -argpos;
   if (o.factor != JAC_FACTOR_CHOL && o.factor != JAC_FACTOR_CHOL_SIGNPIV) return -argpos;
   if (o.precision < JAC_PREC_FP64 || o.precision > JAC_PREC_FP32_ONLY) return -argpos;
   if (batch && o.precision == JAC_PREC_FP32) return -argpos;
@@ -458,6 +458,7 @@ int solve(int m, int n, int dtype, void* Gv, int ldg, const int8_t* Jdev, const 
     pp.tol_m = 0.0;
     pp.factor = o.factor;
     pp.ns_mode = low ? 0 : 1;
+    pp.oriented = (o.block_mode == JAC_BLOCK_ORIENTED) ? 1 : 0;
     if (weights) {
       const int npairs = P.nb * (P.nb - 1) / 2;
       if (!low) {
@@ -784,6 +785,7 @@ int solve_batched(int batch, const int* m, const int* n, int dtype, void* const*
   pp.tol_m = fp32_only ? 8.0 : 0.0;
   pp.factor = o.factor;
   pp.ns_mode = fp32_only ? 0 : 1;
+  pp.oriented = (o.block_mode == JAC_BLOCK_ORIENTED) ? 1 : 0;
   ProfRun prof;
   prof.begin();
   long long launches = 0;

@@ -128,6 +128,7 @@ struct PivotParams {
   double tol_m;
   int factor;        // 0 unpivoted, 2 sign-pivoted
   int ns_mode;       // 1: make V_P J-unitary in FP64 (Newton-Schulz); 0: leave the FP32 transform
+  int oriented;      // 1: block-oriented inner sweep (one sweep; cross block only after step 0)
 };
 
 // per (step, pair) record written by the pivot kernel, reduced per sweep

@@ -13,8 +13,8 @@
 //  4. V_P = P W Pi (rows permuted back as Algorithm 3.4 states; Pi = the reversed order of the
 //     J = -1 columns of Algorithm 3.3), J_P-unitary to FP64 accuracy when requested.
 //
-// GB300 placement.  The inner rotations run in FP32 (warp per column pair, up to 32 pairs at
-// once).  To keep relative precision when A_P is nearly diagonal, the factor is carried as
+// GB300 placement.  The inner rotations run in FP32, LPP lanes per column pair and every pair of
+// an inner step at once, the columns held in registers (see phase 3).  To keep relative precision when A_P is nearly diagonal, the factor is carried as
 //     A_P = D (I + E) D,   R = Dp + F,   W = I + Wd,
 // where D = diag(fp32(sqrt(a_ii))) is fixed and only the deviations F, Wd are stored in FP32:
 // every rotation Q is applied as F <- F Q + Dp (Q - I) and Wd <- Wd Q + (Q - I), so small
@@ -28,67 +28,44 @@
 
 namespace jac {
 
-// Pivot capacity KM (largest k = w_p + w_q of the class), KM / 32 rows of a column per lane,
-// KM / 2 warps (one column pair each).
-template <int KM>
+// Pivot capacity KM (largest k = w_p + w_q of the class); KM / 2 pair slots of LPP lanes each.
+template <int KM, int LPP>
 struct PivotSmem {
   static constexpr int LDF = KM;       // F, W column stride (floats)
   static constexpr int LDS = KM + 1;   // Cholesky matrix / FP32 scratch stride (floats)
   static constexpr int LDV = KM + 1;   // FP64 V / M stride
-  static constexpr int NW = KM / 2;
+  static constexpr int NT = (KM / 2) * LPP;
+  static constexpr int NW = NT / 32;
+  static constexpr int P2 = KM / 2;    // pair slots
+  static constexpr int MBS = 2 * KM + 8;  // mailbox slot: F and W column; +8 floats spreads banks
   double V[KM * LDV];   // A_P first, then V (physical coordinates), FP64
   double M[KM * LDV];   // FP64 residual
   float S[KM * LDS];    // Cholesky working matrix (upper triangle), later FP32 J M
   float F[KM * LDF];
   float W[KM * LDF];
   float Vf[KM * LDS];   // FP32 copy of V for the correction product
-  float cn[KM];         // tracked c_i = ||r_i||^2 - s_i^2 of the inner sweep
+  float mb[2][P2 * MBS];  // column mailboxes of the inner sweep (double-buffered)
+  int mphys[2][P2];
+  float mcn[2][P2];
   float dd[KM];
   float fid[KM];        // fp32(1 / d_i)
   int perm[KM];
   int lpos[KM];
   int jphys[KM];
   int jloc[KM];
+  float dg[2][KM];       // shifted Schur diagonal of the Cholesky steps (double-buffered)
+  int pres[KM / 2];      // block-oriented cross step: columns of block p (pivot order) per slot
+  int ptrav[KM / 2];     // ... and of block q
   float red_f[NW][4];
   int red_i[NW][2];
-  float4 rotp[NW];      // rotation of pair w in the current inner step: q11, q12, q21, q11-1
-  int rflag[NW];
-  float sijv[NW];
   double trs[2];
   int piv;
   int bad;
 };
 
-// a column slice held by one lane: rows lane*R .. lane*R + R - 1
-template <int R>
-struct Slice {
-  float v[R];
-};
-
-template <int R>
-__device__ __forceinline__ Slice<R> load_slice(const float* col, int lane) {
-  Slice<R> x;
-  if (R == 2) {
-    const float2 t = reinterpret_cast<const float2*>(col)[lane];
-    x.v[0] = t.x;
-    x.v[R - 1] = t.y;
-  } else {
-    x.v[0] = col[lane];
-  }
-  return x;
-}
-
-template <int R>
-__device__ __forceinline__ void store_slice(float* col, int lane, const Slice<R>& x) {
-  if (R == 2)
-    reinterpret_cast<float2*>(col)[lane] = make_float2(x.v[0], x.v[R - 1]);
-  else
-    col[lane] = x.v[0];
-}
-
-template <int KM>
-__device__ __forceinline__ float block_max_f(float v, PivotSmem<KM>& sm, int slot) {
-  constexpr int NW = KM / 2;
+template <int KM, int LPP>
+__device__ __forceinline__ float block_max_f(float v, PivotSmem<KM, LPP>& sm, int slot) {
+  constexpr int NW = PivotSmem<KM, LPP>::NW;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -100,11 +77,29 @@ __device__ __forceinline__ float block_max_f(float v, PivotSmem<KM>& sm, int slo
   return r;
 }
 
-template <int KM>
-__global__ void __launch_bounds__(KM * 16, 1)
+// sum over the LPP lanes of a pair slot (aligned lane groups)
+template <int LPP>
+__device__ __forceinline__ float group_sum(float v) {
+#pragma unroll
+  for (int o = LPP / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// entry r of a register-held column (row l R + u in lane l of the group), broadcast to the group;
+// a select chain instead of a dynamic register index
+template <int R>
+__device__ __forceinline__ float col_entry(const float (&f)[R], int r, int group_lane0) {
+  float v = f[0];
+#pragma unroll
+  for (int u = 1; u < R; ++u) v = ((r & (R - 1)) == u) ? f[u] : v;
+  return __shfl_sync(0xffffffffu, v, group_lane0 + r / R);
+}
+
+template <int KM, int LPP>
+__global__ void __launch_bounds__((KM / 2) * LPP, 1)
     k_pivot(const JacProb* __restrict__ probs, int s, PivotParams pp) {
-  constexpr int NT = KM * 16, NW = KM / 2, R = KM / 32;
-  using SM = PivotSmem<KM>;
+  using SM = PivotSmem<KM, LPP>;
+  constexpr int NT = SM::NT, NW = SM::NW;
   constexpr int LDF = SM::LDF, LDS = SM::LDS, LDV = SM::LDV;
   extern __shared__ __align__(16) unsigned char pv_raw[];
   SM& sm = *reinterpret_cast<SM*>(pv_raw);
@@ -239,90 +234,92 @@ __global__ void __launch_bounds__(KM * 16, 1)
   // ---- 2. scaled, optionally sign-pivoted Cholesky in FP32 -----------------------------------
   int npos = 0;
   for (int c = 0; c < k; ++c) npos += (sm.jloc[c] > 0) ? 1 : 0;  // J sorted: + block first
-  if (tid < k) sm.jphys[tid] = sm.jloc[tid];
   __syncthreads();
   const bool signpiv = (pp.factor == 2);
-  // S holds the trailing matrix in its upper triangle: U(a, b) = S[max(a,b) * LDS + min(a,b)]
-  const int cx = tid % KM, cy = tid / KM;  // trailing update: column cx, rows i + 1 + cy + 16 u <= cx
-  for (int i = 0; i < k; ++i) {
-    if (signpiv) {
-      // pivot: the largest unscaled Schur diagonal d_j^2 (1 + s_jj) in the sign group of step i
-      if (warp == 0) {
-        const int hi = (i < npos) ? npos : k;
-        float best = -1.0f;
-        int bj = i;
-        for (int j = i + lane; j < hi; j += 32) {
-          const float dj = sm.dd[j];
-          const float v = dj * dj * (1.0f + sm.S[j * LDS + j]);
-          if (v > best) {
-            best = v;
-            bj = j;
-          }
-        }
+  // Right-looking Cholesky of I + E with diagonal pivoting inside the sign groups, on unpermuted
+  // storage: the trailing entry (a, b), a < b (local indices), stays at S[b * LDS + a]; the pivot
+  // of step i is perm[i]; row i of R~ - I is kept by column index in Fr; the shifted Schur
+  // diagonal s_cc is double-buffered in dg, so that every warp finds the same pivot from the
+  // buffer the previous step completed and one block barrier per step suffices.
+  float* Fr = sm.Vf;  // row i at Fr[i * LDS + c]
+  if (tid < k) sm.dg[0][tid] = sm.S[tid * LDS + tid];
+  // the strictly upper entries (rr, cx), rr < cx < KM, enumerated e = cx (cx - 1) / 2 + rr and
+  // dealt out EPT per thread: every step updates them with independent loads
+  constexpr int NPAIR = KM * (KM - 1) / 2, EPT = (NPAIR + NT - 1) / NT;
+  int ecx[EPT], err_[EPT];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-          const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
-          if (ob > best || (ob == best && oj < bj)) {
-            best = ob;
-            bj = oj;
-          }
-        }
-        if (lane == 0) sm.piv = bj;
+  for (int t = 0; t < EPT; ++t) {
+    const int e = tid + t * NT;
+    int c = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)e)) * 0.5f);
+    while (c * (c - 1) / 2 > e) --c;
+    while ((c + 1) * c / 2 <= e) ++c;
+    ecx[t] = (e < NPAIR) ? c : KM;  // KM: no entry
+    err_[t] = e - c * (c - 1) / 2;
+  }
+  bool live[EPT];  // entry t still in the trailing matrix
+#pragma unroll
+  for (int t = 0; t < EPT; ++t) live[t] = ecx[t] < k;
+  unsigned long long done = 0ull;  // columns already pivoted (identical in every thread)
+  __syncthreads();
+  for (int i = 0; i < k; ++i) {
+    const float* dg = sm.dg[i & 1];
+    float* dgn = sm.dg[(i + 1) & 1];
+    int p = i;
+    if (signpiv) {
+      // the largest unscaled Schur diagonal d_j^2 (1 + s_jj) in the sign group of step i
+      // key: the value's bits above the low 6 (order-preserving for v >= 0) and 63 - j, so one
+      // warp max-reduction yields the largest value, ties to the smaller index; every warp
+      // computes the same key
+      const int lo = (i < npos) ? 0 : npos, hi = (i < npos) ? npos : k;
+      unsigned key = 0u;
+      for (int j = lo + lane; j < hi; j += 32) {
+        if ((done >> j) & 1ull) continue;
+        const float dj = sm.dd[j];
+        const float v = fmaxf(dj * dj * (1.0f + dg[j]), 0.0f);
+        key = max(key, (__float_as_uint(v) & 0xFFFFFFC0u) | (unsigned)(63 - j));
       }
-      __syncthreads();
-      const int pv = sm.piv;
-      if (pv != i) {  // uniform
-        // symmetric swap of rows/columns i and pv of the trailing matrix (upper storage), of
-        // the computed rows of F (columns i and pv), and of the bookkeeping
-        for (int tt = tid; tt < k; tt += NT) {
-          if (tt > i && tt != pv) {
-            const int a1 = tt * LDS + i;
-            const int a2 = (tt > pv) ? tt * LDS + pv : pv * LDS + tt;
-            const float x = sm.S[a1];
-            sm.S[a1] = sm.S[a2];
-            sm.S[a2] = x;
-          }
-          if (tt < i) {
-            const float x = sm.F[i * LDF + tt];
-            sm.F[i * LDF + tt] = sm.F[pv * LDF + tt];
-            sm.F[pv * LDF + tt] = x;
-          }
-        }
-        if (tid == 0) {
-          float x = sm.S[i * LDS + i];
-          sm.S[i * LDS + i] = sm.S[pv * LDS + pv];
-          sm.S[pv * LDS + pv] = x;
-          int y = sm.perm[i];
-          sm.perm[i] = sm.perm[pv];
-          sm.perm[pv] = y;
-          float z = sm.dd[i];
-          sm.dd[i] = sm.dd[pv];
-          sm.dd[pv] = z;
-          y = sm.jphys[i];
-          sm.jphys[i] = sm.jphys[pv];
-          sm.jphys[pv] = y;
-        }
-        __syncthreads();
-      }
+      key = __reduce_max_sync(0xffffffffu, key);
+      p = 63 - (int)(key & 63u);
     }
-    const float sii = sm.S[i * LDS + i];
+    const float sii = dg[p];
     const float piv1 = 1.0f + sii;
-    // The scaled Schur pivot is 1 / (A~^-1)_ii >= 1 / kappa(A~).  Below 64 eps_32 the column is
+    // The scaled Schur pivot is 1 / (A~^-1)_pp >= 1 / kappa(A~).  Below 64 eps_32 the column is
     // in the span of the previous ones at the precision of this factorization: the block goes
     // to the FP64 pivot kernel (which tells an ill-conditioned block from a singular one).
     if (!(piv1 > 3.8146973e-6f)) {
       if (tid == 0) sm.bad = 1;
-      break;  // uniform: every thread read the same sii
+      break;  // uniform: every thread read the same pivot
     }
-    const float r = sqrtf(piv1), ipiv = 1.0f / piv1;
-    // row i of F~ and the trailing update read only row i of S, which this step does not write
-    if (cy == 0 && cx > i && cx < k) sm.F[cx * LDF + i] = sm.S[cx * LDS + i] / r;
-    if (tid == 0) sm.F[i * LDF + i] = sii / (1.0f + r);
-    if (cx > i && cx < k) {
-      const float sil = sm.S[cx * LDS + i] * ipiv;
-      for (int jj = i + 1 + cy; jj <= cx; jj += NT / KM) sm.S[cx * LDS + jj] -= sil * sm.S[jj * LDS + i];
+    done |= 1ull << p;
+    const float rinv = rsqrtf(piv1);  // 1 / r
+    const float r = piv1 * rinv, ipiv = rinv * rinv;
+    // row i of R~ - I (by column index) and the Schur diagonal
+    if (tid < k && !((done >> tid) & 1ull)) {
+      const float spc = sm.S[max(p, tid) * LDS + min(p, tid)];
+      Fr[i * LDS + tid] = spc * rinv;
+      dgn[tid] = dg[tid] - spc * spc * ipiv;
     }
+    if (tid == 0) {
+      Fr[i * LDS + p] = __fdividef(sii, 1.0f + r);
+      sm.perm[i] = p;
+    }
+    // Schur complement of the strictly upper trailing entries; reads touch row p only, which
+    // this step does not write
+    // (all loads first, the old values included, then all stores: no load waits on a store)
+    float nv[EPT];
+    int adr[EPT];
+#pragma unroll
+    for (int t = 0; t < EPT; ++t) {
+      const int c = ecx[t], rr = err_[t];
+      live[t] = live[t] && c != p && rr != p;
+      const int cc = live[t] ? c : 0, rc = live[t] ? rr : 0;  // dead entries read row 0 (in bounds)
+      adr[t] = cc * LDS + rc;
+      const float a = sm.S[max(p, cc) * LDS + min(p, cc)], b = sm.S[max(p, rc) * LDS + min(p, rc)];
+      nv[t] = fmaf(-a * ipiv, b, sm.S[adr[t]]);
+    }
+#pragma unroll
+    for (int t = 0; t < EPT; ++t)
+      if (live[t]) sm.S[adr[t]] = nv[t];
     __syncthreads();
   }
   __syncthreads();
@@ -336,14 +333,42 @@ __global__ void __launch_bounds__(KM * 16, 1)
     }
     return;
   }
-  // R = Dp + F: scale the columns of F~ by dd; logical order of the inner sweep
+  // R = Dp + F in pivot order: F[c][r] = (R~ - I)[r][c] d_c, r <= c; then d and the signs in
+  // pivot order, and the logical order of the inner sweep
   for (int e = tid; e < k * k; e += NT) {
     const int r = e % k, c = e / k;
-    if (r <= c) sm.F[c * LDF + r] *= sm.dd[c];
+    if (r <= c) {
+      const int pc = sm.perm[c];
+      sm.F[c * LDF + r] = Fr[r * LDS + pc] * sm.dd[pc];
+    }
   }
+  float d_new = 0.0f;
+  int j_new = 0;
   if (tid < k) {
-    const int l = tid;
-    sm.lpos[l] = (signpiv && l >= npos) ? (k - 1 - (l - npos)) : l;
+    d_new = sm.dd[sm.perm[tid]];
+    j_new = sm.jloc[sm.perm[tid]];
+  }
+  __syncthreads();
+  // block-oriented steps after the first of a sweep rotate only the cross pairs (one column of
+  // block p, one of block q): block p's columns become the residents of the ring, block q's the
+  // travelers, each in pivot order
+  const bool cross_only = pp.oriented && s > 0;
+  if (tid < SM::P2) {
+    sm.pres[tid] = -1;
+    sm.ptrav[tid] = -1;
+  }
+  __syncthreads();
+  if (tid < k) {
+    sm.dd[tid] = d_new;
+    sm.jphys[tid] = j_new;
+    sm.lpos[tid] = (signpiv && tid >= npos) ? (k - 1 - (tid - npos)) : tid;
+    if (cross_only) {
+      const bool in_p = sm.perm[tid] < wp;
+      int rank = 0;
+      for (int c = 0; c < tid; ++c) rank += ((sm.perm[c] < wp) == in_p) ? 1 : 0;
+      if (in_p) sm.pres[rank] = tid;
+      else sm.ptrav[rank] = tid;
+    }
   }
   __syncthreads();
   const long long t_chol = clock64();
@@ -352,74 +377,81 @@ __global__ void __launch_bounds__(KM * 16, 1)
   // inner threshold: at most half the outer one (so that a pair flagged in FP64 is rotated in
   // FP32), at least the FP32 noise level of the shifted dot products
   const float tol_in = fmaxf(0.5f * tolf, 64.0f * 5.9604645e-8f * mx);
-  const int kk = k + (k & 1);
-  // Each inner step runs in three phases separated by barriers:
-  //   A: warp w forms the dot product r_i^T r_j of its pair (shifted: F_i^T F_j);
-  //   B: warp 0, lane l, forms the rotation of pair l from a_ii, a_jj, a_ij: the scalar 2x2
-  //      work of all pairs shares one instruction stream instead of one per warp;
-  //   C: warp w applies its rotation to the columns of F and W.
-  int total_rot = 0, inner = 0;
-  const int P = kk / 2;
-  for (inner = 0; inner < JAC_INNER_MAX_SWEEPS; ++inner) {
-    // c_i = 2 s_i F_ii + ||f_i||^2 recomputed at the start of every inner sweep, tracked below
-    for (int c = warp; c < k; c += NW) {
-      const Slice<R> f = load_slice<R>(sm.F + c * LDF, lane);
-      float sq = 0.0f;
+  // The columns live in registers: pair slot q (LPP lanes of a warp) holds a resident and a
+  // traveler column, R rows per lane (row l R + u in lane l).  An inner sweep is a recursive
+  // cross ordering of the KM positions: at group size g (KM/2, KM/4, ..., 1 slots) the
+  // travelers of each group go round its ring of g slots, so every resident meets every
+  // traveler of the group in g steps; then each group splits in two, its residents pairing among
+  // themselves in the first half and its travelers in the second.  Every pair of positions
+  // meets once in KM - 1 steps, and between steps each slot passes exactly one column to one
+  // other slot through a shared-memory mailbox: one block barrier per step.  Positions >= k are
+  // empty.  The logical order of Algorithm 3.3 (reversed J = -1 part) gives the initial
+  // placement: position p is the resident of slot p (p < KM/2) or the traveler of slot p - KM/2.
+  constexpr int R = KM / LPP, GP = 32 / LPP, P2 = SM::P2, MBS = SM::MBS;
+  const int grp = lane / LPP, l = lane % LPP, slot = warp * GP + grp, lane0 = grp * LPP;
+  int ci = cross_only ? sm.pres[slot] : ((slot < k) ? sm.lpos[slot] : -1);
+  int cj = cross_only ? sm.ptrav[slot] : ((slot + P2 < k) ? sm.lpos[slot + P2] : -1);
+  // block-oriented: one inner sweep; after the first step of an outer sweep only the ring of
+  // its first level (every column of block p meets every column of block q once)
+  const int g_last = cross_only ? P2 : 1;
+  const int max_inner = pp.oriented ? 1 : JAC_INNER_MAX_SWEEPS;
+  float fi[R], fj[R], wi[R], wj[R];
 #pragma unroll
-      for (int u = 0; u < R; ++u) sq = fmaf(f.v[u], f.v[u], sq);
-      sq = warp_sum(sq);
-      if (lane == 0) sm.cn[c] = 2.0f * sm.dd[c] * sm.F[c * LDF + c] + sq;
-    }
-    __syncthreads();
-    int my_rot = 0;       // warp 0, per lane: rotations of pair `lane` in this sweep
-    float my_max = 0.0f;  // largest scaled |a_ij| rotated
-    for (int st_ = 0; st_ < kk - 1; ++st_) {
-      // ---- A
-      int i = 0, j = 0;
-      bool act = false;
-      Slice<R> fi, fj;
-      if (warp < P) {
-        int li, lj;
-        rr_inner_pair(kk, st_, warp, li, lj);
-        act = lj < k;
-        if (act) {
-          i = sm.lpos[li];
-          j = sm.lpos[lj];
-          fi = load_slice<R>(sm.F + i * LDF, lane);
-          fj = load_slice<R>(sm.F + j * LDF, lane);
-          float sij = 0.0f;
+  for (int u = 0; u < R; ++u) {
+    fi[u] = (ci >= 0) ? sm.F[ci * LDF + l * R + u] : 0.0f;
+    fj[u] = (cj >= 0) ? sm.F[cj * LDF + l * R + u] : 0.0f;
+    wi[u] = 0.0f;
+    wj[u] = 0.0f;
+  }
+  int total_rot = 0, inner = 0, buf = 0;
+  for (inner = 0; inner < max_inner; ++inner) {
+    // c = ||r||^2 - s^2 = 2 s F_cc + ||f||^2 of both columns, recomputed every inner sweep and
+    // tracked through the rotations
+    float cni, cnj;
+    {
+      float qi = 0.0f, qj = 0.0f;
 #pragma unroll
-          for (int u = 0; u < R; ++u) sij = fmaf(fi.v[u], fj.v[u], sij);
-          sij = warp_sum(sij);
-          if (lane == 0) sm.sijv[warp] = sij;
-        }
+      for (int u = 0; u < R; ++u) {
+        qi = fmaf(fi[u], fi[u], qi);
+        qj = fmaf(fj[u], fj[u], qj);
       }
-      __syncthreads();
-      // ---- B
-      if (warp == 0 && lane < P) {
-        int rot = 0;
-        float4 rp = make_float4(0.f, 0.f, 0.f, 0.f);
-        int li, lj;
-        rr_inner_pair(kk, st_, lane, li, lj);
-        if (lj < k) {
-          const int bi = sm.lpos[li], bj = sm.lpos[lj];
-          const float si = sm.dd[bi], sj = sm.dd[bj];
-          const float ci = sm.cn[bi], cj = sm.cn[bj];
-          const float aij = si * sm.F[bj * LDF + bi] + sj * sm.F[bi * LDF + bj] + sm.sijv[lane];
-          const float aii = fmaf(si, si, ci), ajj = fmaf(sj, sj, cj);
+      qi = group_sum<LPP>(qi);
+      qj = group_sum<LPP>(qj);
+      const float di = col_entry<R>(fi, ci >= 0 ? ci : 0, lane0);
+      const float dj = col_entry<R>(fj, cj >= 0 ? cj : 0, lane0);
+      cni = (ci >= 0) ? 2.0f * sm.dd[ci] * di + qi : 0.0f;
+      cnj = (cj >= 0) ? 2.0f * sm.dd[cj] * dj + qj : 0.0f;
+    }
+    int my_rot = 0;       // per slot (uniform over its lanes)
+    float my_max = 0.0f;  // largest scaled |a_ij| rotated
+    for (int g = P2; g >= g_last; g >>= 1) {
+      const int base = slot & ~(g - 1), pos = slot - base;
+      for (int st_ = 0; st_ < g; ++st_) {
+        // ---- rotate the pair (ci, cj) of this slot
+        const bool act = (ci >= 0) && (cj >= 0);
+        const int ii = act ? ci : 0, jj = act ? cj : 0;
+        float sij = 0.0f;
+#pragma unroll
+        for (int u = 0; u < R; ++u) sij = fmaf(fi[u], fj[u], sij);
+        sij = group_sum<LPP>(sij);
+        const float fji = col_entry<R>(fj, ii, lane0);  // F_ij: row i of column j
+        const float fij = col_entry<R>(fi, jj, lane0);  // F_ji
+        if (act) {
+          const float si = sm.dd[ii], sj = sm.dd[jj];
+          const float aij = si * fji + sj * fij + sij;
+          const float aii = fmaf(si, si, cni), ajj = fmaf(sj, sj, cnj);
           const float beta = fabsf(aij);
           const float scaled = beta * rsqrtf(aii) * rsqrtf(ajj);
           if (scaled > tol_in) {
-            rot = 1;
             ++my_rot;
             my_max = fmaxf(my_max, scaled);
             const float e = (aij < 0.0f) ? -1.0f : 1.0f;
-            float dci, dcj;
-            if (sm.jphys[bi] == sm.jphys[bj]) {
+            float q11, q12, q21, cm1, dci, dcj;
+            if (sm.jphys[ii] == sm.jphys[jj]) {
               // trigonometric, Eq. (2.1): cot(2 phi) = (a_jj - a_ii) / (2 |a_ij|), i.e.
               // t = sign(a_jj - a_ii) 2|a_ij| / (|a_jj - a_ii| + sqrt((a_jj - a_ii)^2 + 4|a_ij|^2)),
               // evaluated after an exact power-of-two scaling of both terms into [1, 4)
-              const float num = (sj - si) * (sj + si) + (cj - ci);
+              const float num = (sj - si) * (sj + si) + (cnj - cni);
               const float mxv = fmaxf(fabsf(num), 2.0f * beta);
               const float sc = __int_as_float(0x7f000000 - (__float_as_int(mxv) & 0x7f800000));
               const float nu = num * sc, b2 = 2.0f * beta * sc;
@@ -427,7 +459,10 @@ __global__ void __launch_bounds__(KM * 16, 1)
               const float t = copysignf(__fdividef(b2, den), num);
               const float c = rsqrtf(fmaf(t, t, 1.0f));
               const float s_ = t * c;
-              rp = make_float4(c, e * s_, -e * s_, -__fdividef(s_ * s_, 1.0f + c));
+              q11 = c;
+              q12 = e * s_;
+              q21 = -e * s_;
+              cm1 = -__fdividef(s_ * s_, 1.0f + c);
               dci = -t * beta;  // a_ii' = a_ii - t |a_ij|, a_jj' = a_jj + t |a_ij|
               dcj = t * beta;
             } else {
@@ -442,80 +477,113 @@ __global__ void __launch_bounds__(KM * 16, 1)
               if (!(fabsf(t) < 1.0f) || !((1.0f - t) * (1.0f + t) > 0.0f)) t = copysignf(0.9f, t);
               const float ch = rsqrtf((1.0f - t) * (1.0f + t));
               const float sh = t * ch;
-              rp = make_float4(ch, e * sh, e * sh, __fdividef(sh * sh, 1.0f + ch));
+              q11 = ch;
+              q12 = e * sh;
+              q21 = e * sh;
+              cm1 = __fdividef(sh * sh, 1.0f + ch);
               dci = t * beta;  // both diagonals move by t |a_ij| (the J-trace is invariant)
               dcj = t * beta;
             }
-            sm.cn[bi] = ci + dci;
-            sm.cn[bj] = cj + dcj;
+            // F <- F Q + Dp (Q - I), Wd <- Wd Q + (Q - I): the Dp (Q - I) / (Q - I) terms touch
+            // rows i and j only
+#pragma unroll
+            for (int u = 0; u < R; ++u) {
+              const int row = l * R + u;
+              const float a_i = fi[u], a_j = fj[u], b_i = wi[u], b_j = wj[u];
+              float nfi = fmaf(q11, a_i, q21 * a_j), nfj = fmaf(q11, a_j, q12 * a_i);
+              float nwi = fmaf(q11, b_i, q21 * b_j), nwj = fmaf(q11, b_j, q12 * b_i);
+              if (row == ii) {
+                nfi += si * cm1;
+                nfj += si * q12;
+                nwi += cm1;
+                nwj += q12;
+              }
+              if (row == jj) {
+                nfi += sj * q21;
+                nfj += sj * cm1;
+                nwi += q21;
+                nwj += cm1;
+              }
+              fi[u] = nfi;
+              fj[u] = nfj;
+              wi[u] = nwi;
+              wj[u] = nwj;
+            }
+            cni += dci;
+            cnj += dcj;
           }
         }
-        sm.rotp[lane] = rp;
-        sm.rflag[lane] = rot;
-      }
-      __syncthreads();
-      // ---- C
-      if (act && sm.rflag[warp]) {
-        const float4 rp = sm.rotp[warp];
-        const float q11 = rp.x, q12 = rp.y, q21 = rp.z, cm1 = rp.w;
-        const float si = sm.dd[i], sj = sm.dd[j];
-        Slice<R> nfi, nfj;
+        // ---- pass one column on: the traveler round the ring, or at the end of the group's
+        // ring its split (first half: traveler to slot + g/2, which sends back its resident)
+        if (st_ < g - 1 || g > g_last) {
+          const bool ring = st_ < g - 1;
+          const bool give_res = !ring && pos >= g / 2;  // second half of a split sends its resident
+          const int dst = ring ? base + ((pos + 1) & (g - 1)) : (pos < g / 2 ? slot + g / 2 : slot - g / 2);
+          float* box = sm.mb[buf] + dst * MBS + l * R;
 #pragma unroll
-        for (int u = 0; u < R; ++u) {
-          nfi.v[u] = fmaf(q11, fi.v[u], q21 * fj.v[u]);
-          nfj.v[u] = fmaf(q11, fj.v[u], q12 * fi.v[u]);
-        }
-        // + Dp (Q - I): column i gets si (q11-1) at row i and sj q21 at row j; column j
-        // gets si q12 at row i and sj (q22-1) at row j
-        if (lane == i / R) {
-          nfi.v[i % R] += si * cm1;
-          nfj.v[i % R] += si * q12;
-        }
-        if (lane == j / R) {
-          nfi.v[j % R] += sj * q21;
-          nfj.v[j % R] += sj * cm1;
-        }
-        store_slice<R>(sm.F + i * LDF, lane, nfi);
-        store_slice<R>(sm.F + j * LDF, lane, nfj);
-        const Slice<R> wi = load_slice<R>(sm.W + i * LDF, lane), wj = load_slice<R>(sm.W + j * LDF, lane);
-        Slice<R> nwi, nwj;
+          for (int u = 0; u < R; ++u) {
+            box[u] = give_res ? fi[u] : fj[u];
+            box[KM + u] = give_res ? wi[u] : wj[u];
+          }
+          if (l == 0) {
+            sm.mphys[buf][dst] = give_res ? ci : cj;
+            sm.mcn[buf][dst] = give_res ? cni : cnj;
+          }
+          __syncthreads();
+          const float* in = sm.mb[buf] + slot * MBS + l * R;
+          const int cin = sm.mphys[buf][slot];
+          const float cnin = sm.mcn[buf][slot];
+          if (give_res) {
 #pragma unroll
-        for (int u = 0; u < R; ++u) {
-          nwi.v[u] = fmaf(q11, wi.v[u], q21 * wj.v[u]);
-          nwj.v[u] = fmaf(q11, wj.v[u], q12 * wi.v[u]);
+            for (int u = 0; u < R; ++u) {
+              fi[u] = in[u];
+              wi[u] = in[KM + u];
+            }
+            ci = cin;
+            cni = cnin;
+          } else {
+#pragma unroll
+            for (int u = 0; u < R; ++u) {
+              fj[u] = in[u];
+              wj[u] = in[KM + u];
+            }
+            cj = cin;
+            cnj = cnin;
+          }
+          buf ^= 1;
         }
-        if (lane == i / R) {
-          nwi.v[i % R] += cm1;
-          nwj.v[i % R] += q12;
-        }
-        if (lane == j / R) {
-          nwi.v[j % R] += q21;
-          nwj.v[j % R] += cm1;
-        }
-        store_slice<R>(sm.W + i * LDF, lane, nwi);
-        store_slice<R>(sm.W + j * LDF, lane, nwj);
       }
-      __syncthreads();
     }
-    if (warp == 0) {
-      const int tot_w = warp_sum_i(my_rot);
+    // sweep totals: one count per slot (its lane 0)
+    int cnt = (l == 0) ? my_rot : 0;
+    cnt = warp_sum_i(cnt);
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) my_max = fmaxf(my_max, __shfl_xor_sync(0xffffffffu, my_max, o));
-      if (lane == 0) {
-        sm.red_i[0][1] = tot_w;
-        sm.red_f[0][2] = my_max;
-      }
+    for (int o = 16; o > 0; o >>= 1) my_max = fmaxf(my_max, __shfl_xor_sync(0xffffffffu, my_max, o));
+    if (lane == 0) {
+      sm.red_i[warp][1] = cnt;
+      sm.red_f[warp][2] = my_max;
     }
     __syncthreads();
-    const int tot = sm.red_i[0][1];
-    const float dmax = sm.red_f[0][2];
+    int tot = 0;
+    float dmax = 0.0f;
+    for (int w = 0; w < NW; ++w) {
+      tot += sm.red_i[w][1];
+      dmax = fmaxf(dmax, sm.red_f[w][2]);
+    }
     __syncthreads();
     total_rot += tot;
     // done when nothing was rotated, or when every rotated pair was already so small that the
     // next sweep (quadratic convergence: off-diagonals ~ k delta^2) would find nothing above tol_in
     if (tot == 0 || (float)k * dmax * dmax <= tol_in) break;
   }
-  if (inner >= JAC_INNER_MAX_SWEEPS && tid == 0) atomicOr(err, JAC_DEVERR_INNER_LIMIT);
+  if (!pp.oriented && inner >= JAC_INNER_MAX_SWEEPS && tid == 0) atomicOr(err, JAC_DEVERR_INNER_LIMIT);
+  // W columns back to shared memory, physical coordinates
+#pragma unroll
+  for (int u = 0; u < R; ++u) {
+    if (ci >= 0) sm.W[ci * LDF + l * R + u] = wi[u];
+    if (cj >= 0) sm.W[cj * LDF + l * R + u] = wj[u];
+  }
+  __syncthreads();
   const long long t_inner = clock64();
 
   // ---- 4. V = I + Wd (physical coordinates), J-orthogonalized in FP64 if requested ----------
@@ -532,7 +600,7 @@ __global__ void __launch_bounds__(KM * 16, 1)
   bool ns_ok = true;
   if (pp.ns_mode) {
     ns_ok = false;
-    wm = block_max_f<KM>(wm, sm, 3);  // includes the barrier after the V build
+    wm = block_max_f<KM, LPP>(wm, sm, 3);  // includes the barrier after the V build
     const bool small_w = wm <= 9.5367431640625e-7f;  // 2^-20
     for (int it = 0; it < 3; ++it) {
       // residual M = V^T J V - J, J = diag(jphys) on rows and columns
@@ -591,7 +659,7 @@ __global__ void __launch_bounds__(KM * 16, 1)
           sm.S[j * LDS + x] = (x < k) ? (float)((sm.jphys[x] < 0) ? -mv : mv) : 0.0f;
         }
       }
-      const float mm = block_max_f<KM>(mloc, sm, 0);
+      const float mm = block_max_f<KM, LPP>(mloc, sm, 0);
       if (mm <= 4.0e-16f) {
         ns_ok = true;
         break;
@@ -624,7 +692,7 @@ __global__ void __launch_bounds__(KM * 16, 1)
     if (tid == 0) {
       a.skip[pair] = 2;
       st.rotations = total_rot;
-      st.inner_sweeps = inner + 1;
+      st.inner_sweeps = (inner < max_inner) ? inner + 1 : max_inner;
       st.ns_steps = ns;
       st.cyc[0] = t_stats - t_start;
       st.cyc[1] = t_chol - t_stats;
@@ -649,7 +717,7 @@ __global__ void __launch_bounds__(KM * 16, 1)
   if (tid == 0) {
     a.skip[pair] = 0;
     st.rotations = total_rot;
-    st.inner_sweeps = inner + 1;
+    st.inner_sweeps = (inner < max_inner) ? inner + 1 : max_inner;
     st.ns_steps = ns;
     st.cyc[0] = t_stats - t_start;
     st.cyc[1] = t_chol - t_stats;
@@ -659,24 +727,32 @@ __global__ void __launch_bounds__(KM * 16, 1)
   }
 }
 
-size_t pivot_smem_bytes(int km) { return km == 32 ? sizeof(PivotSmem<32>) : sizeof(PivotSmem<64>); }
+// Lanes per pair slot of each pivot capacity: KM = 64 -> 8 lanes x 8 rows, 256 threads;
+// KM = 32 -> 8 lanes x 4 rows, 128 threads.
+constexpr int kLpp64 = 8, kLpp32 = 8;
+
+size_t pivot_smem_bytes(int km) {
+  return km == 32 ? sizeof(PivotSmem<32, kLpp32>) : sizeof(PivotSmem<64, kLpp64>);
+}
 
 // Host side of the two instantiations (a kernel template is launched from its own translation unit).
 int pivot_set_attributes() {
-  bool ok = cudaFuncSetAttribute(k_pivot<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)sizeof(PivotSmem<32>)) == cudaSuccess;
-  ok &= cudaFuncSetAttribute(k_pivot<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PivotSmem<64>)) ==
-        cudaSuccess;
+  bool ok = cudaFuncSetAttribute(k_pivot<32, kLpp32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(PivotSmem<32, kLpp32>)) == cudaSuccess;
+  ok &= cudaFuncSetAttribute(k_pivot<64, kLpp64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(PivotSmem<64, kLpp64>)) == cudaSuccess;
   return ok ? 0 : 1;
 }
 
-// Grid (max_half, nprob): one CTA of km*16 threads per pivot block.
+// Grid (max_half, nprob): one CTA per pivot block.
 void pivot_launch(int km, int max_half, int nprob, cudaStream_t st, const JacProb* probs, int s,
                   const PivotParams& pp) {
   if (km == 32)
-    k_pivot<32><<<dim3(max_half, nprob), 32 * 16, sizeof(PivotSmem<32>), st>>>(probs, s, pp);
+    k_pivot<32, kLpp32><<<dim3(max_half, nprob), PivotSmem<32, kLpp32>::NT, sizeof(PivotSmem<32, kLpp32>), st>>>(
+        probs, s, pp);
   else
-    k_pivot<64><<<dim3(max_half, nprob), 64 * 16, sizeof(PivotSmem<64>), st>>>(probs, s, pp);
+    k_pivot<64, kLpp64><<<dim3(max_half, nprob), PivotSmem<64, kLpp64>::NT, sizeof(PivotSmem<64, kLpp64>), st>>>(
+        probs, s, pp);
 }
 
 }  // namespace jac

@@ -63,6 +63,24 @@ def test_config2_mixed_precision(cuda_dev, ordering, factor):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("ordering", ["round_robin", "cycle_weight", "modulus_mod"])
+def test_block_oriented(cuda_dev, precision, ordering):
+    """Block-oriented HB/HBSC (Sec. 2.2, Algorithm 3.4): one inner sweep per pivot block, the
+    cross block only after the first step of a sweep; same tolerances."""
+    from paper_1008_0201_gb300 import inputs
+
+    G, J = inputs.config2_hyperbolic()
+    out = run(G, J, cuda_dev, block_w=32, ordering=ordering, block_mode="oriented", precision=precision)
+    assert out["status"] == 0, out["info"]
+    r = compare(G, J, out)
+    print("C2-oriented", ordering, precision, out["info"]["sweeps"], r)
+    G1, J1 = inputs.config1_pd()
+    out1 = run(G1, None, cuda_dev, block_w=8, ordering=ordering, block_mode="oriented", precision=precision)
+    assert out1["status"] == 0, out1["info"]
+    compare(G1, J1, out1)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_config1_precisions(cuda_dev, precision):
     from paper_1008_0201_gb300 import inputs
 
