@@ -137,7 +137,12 @@ int jacobi_version(void);
  * Sec. 3.2, Algorithm 3.4 (full block; Cholesky per opts->factor, Algorithm 3.3).
  *
  *  1 m, 2 n        G is m x n, m >= n >= 1 (full column rank required when J != I).
- *  3 dtype         JAC_R64 (JAC_C128 is rejected with -3 in this version).
+ *  3 dtype         JAC_R64 or JAC_C128 (G, U, V interleaved (re, im) doubles, leading
+ *                  dimensions in complex elements; n <= 10000).  A complex problem is solved
+ *                  as the real one of twice the order, G_r = [X -Y; Y X] for G = X + iY and
+ *                  J_r = diag(J, J), whose spectrum is that of H twice; the complex results are
+ *                  read off every other column (JAC_EINTERNAL if the two copies of an eigenvalue
+ *                  differ by more than 1e-6 relative).
  *  4 G, 5 ldg      device, in/out.  On return G = G_in V: the unnormalized U Sigma, columns in
  *                  output order.
  *  6 J             device int8[n], entries +1 / -1, any order (sorted internally to

@@ -128,8 +128,10 @@ def _check_cuda(t, name):
 
 
 def _colmajor(G):
-    """Column-major (Fortran-order) float64 view/copy of a 2-D tensor, as the C ABI expects."""
-    Gt = G.to(torch.float64).t().contiguous()  # (n, m) row-major == (m, n) column-major
+    """Column-major (Fortran-order) float64 / complex128 copy of a 2-D tensor, as the C ABI
+    expects (complex: interleaved (re, im) doubles)."""
+    dt = torch.complex128 if G.is_complex() else torch.float64
+    Gt = G.to(dt).t().contiguous()  # (n, m) row-major == (m, n) column-major
     return Gt
 
 
@@ -142,10 +144,11 @@ def _call(fn_name, G, J, opts, want_u, raise_on_error):
     if opts is None:
         opts = default_opts()
     lam = torch.empty(n, dtype=torch.float64, device=dev)
-    Ut = torch.empty((n, m), dtype=torch.float64, device=dev) if want_u else None
-    Vt = torch.empty((n, n), dtype=torch.float64, device=dev) if opts.want_v else None
+    cplx = Gt.is_complex()
+    Ut = torch.empty((n, m), dtype=Gt.dtype, device=dev) if want_u else None
+    Vt = torch.empty((n, n), dtype=Gt.dtype, device=dev) if opts.want_v else None
     info = JacInfo()
-    args = [m, n, JAC_R64, ctypes.c_void_p(Gt.data_ptr()), m]
+    args = [m, n, JAC_C128 if cplx else JAC_R64, ctypes.c_void_p(Gt.data_ptr()), m]
     if fn_name == "jacobi_hsvd":
         _check_cuda(J, "J")
         Jd = J.to(device=dev, dtype=torch.int8).contiguous()

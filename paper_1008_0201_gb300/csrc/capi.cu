@@ -49,6 +49,10 @@ __global__ void k_cvt64to32(int rows, int cols, const double* src, int lds, floa
 __global__ void k_cvt32to64(int rows, int cols, const float* src, int lds, double* dst, int ldd);
 __global__ void k_absmax64(int n, const double* M, int ldm, unsigned long long* out);
 __global__ void k_lowp_copy(const JacProb* probs, int to64);
+__global__ void k_realify(int m, int n, const double2* G, int ldg, const int8_t* J, double* Gr, int8_t* Jr);
+__global__ void k_complexify(int m, int n, const double* Gr, const double* lam_r, const double* Vr, double2* G, int ldg,
+                             double* lambda, double2* U, int ldu, double2* V, int ldv, unsigned* bad);
+__global__ void k_restructure(int h, int n, const double* in, double* out, const double* lam, int8_t* Jout);
 }  // namespace jac
 
 using namespace jac;
@@ -309,8 +313,9 @@ struct Single {
 };
 
 // ------------------------------------------------------------------ single solve
-int solve(int m, int n, int dtype, void* Gv, int ldg, const int8_t* Jdev, const jac_opts* opts_in, double* lambda,
-          void* Uv, int ldu, void* Vv, int ldv, jac_info* info, cudaStream_t st, const ArgPos& ap) {
+int solve_real(int m, int n, int dtype, void* Gv, int ldg, const int8_t* Jdev, const jac_opts* opts_in, double* lambda,
+               void* Uv, int ldu, void* Vv, int ldv, jac_info* info, cudaStream_t st, const ArgPos& ap,
+               const double* Vinit = nullptr) {
   jac_opts o;
   jacobi_default_opts(&o);
   if (opts_in) o = *opts_in;
@@ -393,6 +398,8 @@ int solve(int m, int n, int dtype, void* Gv, int ldg, const int8_t* Jdev, const 
   hio.ldu = ldu;
   hio.V = want_v ? static_cast<double*>(Vv) : nullptr;
   hio.ldv = ldv;
+  hio.Vinit = Vinit;
+  hio.ldvi = n;
 
   int status = JAC_OK;
   auto ck = [&](cudaError_t e) {
@@ -593,6 +600,133 @@ int solve(int m, int n, int dtype, void* Gv, int ldg, const int8_t* Jdev, const 
     info->inner_sweeps = inner_total;
   }
   return status;
+}
+
+// ------------------------------------------------------------------ complex solve
+// A complex problem is solved as the real problem of twice the order (complex.cu); the complex
+// results are read off every other column of the ascending real result.
+int solve_complex(int m, int n, void* Gv, int ldg, const int8_t* Jdev, const jac_opts* opts_in, double* lambda,
+                  void* Uv, int ldu, void* Vv, int ldv, jac_info* info, cudaStream_t st, const ArgPos& ap) {
+  jac_opts o;
+  jacobi_default_opts(&o);
+  if (opts_in) o = *opts_in;
+  if (info) std::memset(info, 0, sizeof(*info));
+  auto fail_arg = [&](int pos) {
+    if (info) info->status = -pos;
+    return -pos;
+  };
+  if (m < 1) return fail_arg(ap.m);
+  if (n < 1 || n > m || n > 10000) return fail_arg(ap.n);
+  if (!Gv) return fail_arg(ap.G);
+  if (ldg < m) return fail_arg(ap.ldg);
+  if (ap.J && !Jdev) return fail_arg(ap.J);
+  if (int r = check_opts(o, ap.opts, false)) return fail_arg(-r);
+  if (!lambda) return fail_arg(ap.lambda);
+  if (Uv && ldu < m) return fail_arg(ap.ldu);
+  if (Uv && Uv == Gv) return fail_arg(ap.U);
+  if (o.want_v && !Vv) return fail_arg(ap.V);
+  if (Vv && ldv < n) return fail_arg(ap.ldv);
+  const bool want_v = o.want_v != 0;
+  // the rotation threshold is that of the complex problem of order n (tol <= 0: n eps), not of
+  // the real one of order 2n: both copies of a complex column pair are then orthogonal to the
+  // other columns to the complex problem's tolerance
+  if (o.tol <= 0.0)
+    o.tol = (o.precision == JAC_PREC_FP32_ONLY) ? std::max((double)n, 8.0 * std::sqrt((double)m)) * 5.9604644775390625e-08
+                                                : (double)n * 1.1102230246251565e-16;
+  const size_t m2 = 2 * (size_t)m, n2 = 2 * (size_t)n;
+  double *Gr = nullptr, *Gr2 = nullptr, *lam_r = nullptr, *Vr = nullptr, *Vr2 = nullptr;
+  int8_t *Jr = nullptr, *Jr2 = nullptr;
+  unsigned* bad = nullptr;
+  auto carve = [&](Arena& A) {
+    Jr2 = A.take<int8_t>(n2);
+    Gr = A.take<double>(m2 * n2);
+    Gr2 = A.take<double>(m2 * n2);
+    lam_r = A.take<double>(n2);
+    Vr = want_v ? A.take<double>(n2 * n2) : nullptr;
+    Vr2 = want_v ? A.take<double>(n2 * n2) : nullptr;
+    Jr = A.take<int8_t>(n2);
+    bad = A.take<unsigned>(1);
+  };
+  Arena ar;
+  carve(ar);
+  void* base = nullptr;
+  if (cudaMallocAsync(&base, ar.off, st) != cudaSuccess) {
+    cudaGetLastError();
+    if (info) info->status = JAC_ENOMEM;
+    return JAC_ENOMEM;
+  }
+  Arena ar2;
+  ar2.base = static_cast<char*>(base);
+  carve(ar2);
+  int status = JAC_OK;
+  if (cudaMemsetAsync(bad, 0, sizeof(unsigned), st) != cudaSuccess) status = JAC_ECUDA;
+  const int eb = (int)std::min<size_t>(4096, ((size_t)m * n + 255) / 256);
+  k_realify<<<eb, 256, 0, st>>>(m, n, static_cast<const double2*>(Gv), ldg, Jdev, Gr, Jr);
+  if (cudaGetLastError() != cudaSuccess) status = JAC_ECUDA;
+  // pass 1: the sweep as requested
+  if (status == JAC_OK)
+    status = solve_real((int)m2, (int)n2, JAC_R64, Gr, (int)m2, Jr, &o, lam_r, nullptr, 0, Vr, (int)n2, info, st, ap);
+  jac_info info1 = {};
+  if (info) info1 = *info;
+  double* Gres = Gr;
+  double* Vres = Vr;
+  // pass 2 (FP64, or FP32 for the FP32-only form): exact pairs from pass 1, started from its V
+  if (status == JAC_OK) {
+    const int eb2 = (int)std::min<size_t>(4096, (m2 * n + 255) / 256);
+    k_restructure<<<eb2, 256, 0, st>>>(m, n, Gr, Gr2, lam_r, Jr2);  // signs of the output columns
+    if (want_v)
+      k_restructure<<<(int)std::min<size_t>(4096, (n2 * n + 255) / 256), 256, 0, st>>>(n, n, Vr, Vr2, nullptr, nullptr);
+    if (cudaGetLastError() != cudaSuccess) status = JAC_ECUDA;
+    jac_opts o2 = o;
+    if (o2.precision == JAC_PREC_FP32) o2.precision = JAC_PREC_FP64;
+    if (status == JAC_OK)
+      status = solve_real((int)m2, (int)n2, JAC_R64, Gr2, (int)m2, Jr2, &o2, lam_r, nullptr, 0, Vr, (int)n2, info, st, ap,
+                          want_v ? Vr2 : nullptr);
+    if (info) {  // totals over both passes; the per-sweep maxima of pass 1, then of pass 2
+      double merged[64];
+      int t = 0;
+      for (int u = 0; u < info1.sweeps && u < 64 && t < 64; ++u) merged[t++] = info1.sweep_max_scaled[u];
+      for (int u = 0; u < info->sweeps && u < 64 && t < 64; ++u) merged[t++] = info->sweep_max_scaled[u];
+      while (t < 64) merged[t++] = 0.0;
+      for (int u = 0; u < 64; ++u) info->sweep_max_scaled[u] = merged[u];
+      info->sweeps += info1.sweeps;
+      info->rotations += info1.rotations;
+      info->pivots_rotated += info1.pivots_rotated;
+      info->launches += info1.launches + 2;
+      info->lowp_sweeps += info1.lowp_sweeps;
+      info->global_ns_steps += info1.global_ns_steps;
+      info->pivot_ns_steps += info1.pivot_ns_steps;
+      info->inner_sweeps += info1.inner_sweeps;
+      for (int u = 0; u < 4; ++u) info->pivot_cycles[u] += info1.pivot_cycles[u];
+    }
+    Gres = Gr2;
+  }
+  if (status == JAC_OK || status == JAC_ENOTCONV) {
+    k_complexify<<<dim3((m + 127) / 128, n), 128, 0, st>>>(m, n, Gres, lam_r, Vres, static_cast<double2*>(Gv), ldg,
+                                                          lambda, static_cast<double2*>(Uv), ldu,
+                                                          want_v ? static_cast<double2*>(Vv) : nullptr, ldv, bad);
+    unsigned hbad = 0;
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(&hbad, bad, sizeof(unsigned), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+      status = JAC_ECUDA;
+    cudaFreeAsync(base, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) status = JAC_ECUDA;
+    if (status == JAC_OK && hbad) status = JAC_EINTERNAL;
+    if (info) {
+      info->status = status;
+      info->launches += 1;
+    }
+    return status;
+  }
+  cudaFreeAsync(base, st);
+  cudaStreamSynchronize(st);
+  return status;
+}
+
+int solve(int m, int n, int dtype, void* Gv, int ldg, const int8_t* Jdev, const jac_opts* opts_in, double* lambda,
+          void* Uv, int ldu, void* Vv, int ldv, jac_info* info, cudaStream_t st, const ArgPos& ap) {
+  if (dtype == JAC_C128) return solve_complex(m, n, Gv, ldg, Jdev, opts_in, lambda, Uv, ldu, Vv, ldv, info, st, ap);
+  return solve_real(m, n, dtype, Gv, ldg, Jdev, opts_in, lambda, Uv, ldu, Vv, ldv, info, st, ap);
 }
 
 // ------------------------------------------------------------------ batched solve

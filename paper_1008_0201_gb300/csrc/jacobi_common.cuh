@@ -113,6 +113,8 @@ struct JacIO {
   int ldu;
   double* V;           // may be NULL
   int ldv;
+  const double* Vinit; // NULL: V starts as I; else V starts as this n x n matrix (ld ldvi)
+  int ldvi;
   double* nrm2;        // [n] scratch
   double* lam;         // [n] scratch
   int* rank;           // [n] scratch

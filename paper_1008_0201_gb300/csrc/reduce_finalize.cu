@@ -156,14 +156,18 @@ __global__ void k_gather_in(const JacProb* __restrict__ probs, const JacIO* __re
   a.Gw[(size_t)c * a.mp + r] = (r < o.m) ? o.G[(size_t)src * o.ldg + r] : 0.0;
 }
 
-// Vw = Pi (the internal column order): Vw[perm_in[c], c] = 1.  Grid (ceil(np/256), n, nprob).
+// Vw = Pi (the internal column order): Vw[perm_in[c], c] = 1; or, with a starting transform,
+// Vw = Vinit Pi.  Grid (ceil(np/256), n, nprob).
 __global__ void k_init_v(const JacProb* __restrict__ probs, const JacIO* __restrict__ io) {
   const JacProb& a = probs[blockIdx.z];
   const JacIO& o = io[blockIdx.z];
   const int c = blockIdx.y;
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (!a.Vw || c >= a.n || r >= a.np) return;
-  a.Vw[(size_t)c * a.np + r] = (r < a.n && r == o.perm_in[c]) ? 1.0 : 0.0;
+  double v;
+  if (o.Vinit) v = (r < a.n) ? o.Vinit[(size_t)o.perm_in[c] * o.ldvi + r] : 0.0;
+  else v = (r < a.n && r == o.perm_in[c]) ? 1.0 : 0.0;
+  a.Vw[(size_t)c * a.np + r] = v;
 }
 
 // Sets JAC_DEVERR_NONFINITE (and, per problem, io.flags bit 0) if an entry of G has an all-ones

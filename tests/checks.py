@@ -66,7 +66,7 @@ def compare(G0, J, out, ref=None, check_vectors=True, kappa=None, eps=EPS):
             relgap = gaps.min()
             u = U[:, i] / np.linalg.norm(U[:, i])
             v = Ur[:, i] / np.linalg.norm(Ur[:, i])
-            s = np.linalg.norm(u - np.dot(u, v) * v)  # sin of the angle, no 1 - cos^2 cancellation
+            s = np.linalg.norm(u - np.vdot(v, u) * v)  # sin of the angle (any complex phase)
             bound = 50 * n * eps * kappa / relgap + 1e-14
             assert s <= bound, ("eigenvector", i, s, bound)
             if np.isfinite(relgap):

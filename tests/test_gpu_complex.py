@@ -1,0 +1,83 @@
+"""Complex Hermitian problems (dtype JAC_C128) through the C ABI against the complex oracle.
+
+Inputs are seeded complex Gaussian factors, positive definite and indefinite, and scaled-down
+copies of the graded workload G = B D (B complex Gaussian, D = diag(10^(-8 i / n))); every
+result is held to the same tolerances as the real problems (tests/checks.py).
+"""
+import numpy as np
+import pytest
+
+from checks import compare, to_np
+
+pytestmark = pytest.mark.gpu
+
+
+def run(G, J, dev, **kw):
+    import torch
+
+    from paper_1008_0201_gb300 import binding
+
+    opts = binding.default_opts(**kw)
+    Gd = torch.from_numpy(np.ascontiguousarray(G)).to(dev)
+    if J is None:
+        out = binding.jacobi_eig_pd(Gd, opts, raise_on_error=False)
+    else:
+        out = binding.jacobi_hsvd(Gd, torch.from_numpy(J).to(dev), opts, raise_on_error=False)
+    torch.cuda.synchronize()
+    return to_np(out)
+
+
+def cgauss(g, m, n):
+    return (g.standard_normal((m, n)) + 1j * g.standard_normal((m, n))) * np.sqrt(0.5)
+
+
+@pytest.mark.parametrize("m,n,w", [(24, 24, 4), (48, 48, 8), (70, 45, 8)])
+def test_complex_pd(cuda_dev, m, n, w):
+    g = np.random.default_rng(300 + n)
+    G = cgauss(g, m, n)
+    out = run(G, None, cuda_dev, block_w=w)
+    assert out["status"] == 0, out["info"]
+    assert out["G"].dtype == np.complex128 and out["V"].dtype == np.complex128
+    compare(G, np.ones(n, dtype=np.int8), out)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("block_mode", ["full", "oriented"])
+def test_complex_hyperbolic(cuda_dev, precision, block_mode):
+    g = np.random.default_rng(311)
+    m, n = 60, 40
+    G = cgauss(g, m, n)
+    J = np.ones(n, dtype=np.int8)
+    J[g.choice(n, size=15, replace=False)] = -1
+    out = run(G, J, cuda_dev, block_w=8, precision=precision, block_mode=block_mode)
+    assert out["status"] == 0, out["info"]
+    compare(G, J, out)
+
+
+@pytest.mark.parametrize("n,w", [(64, 16), (128, 32)])
+def test_complex_graded(cuda_dev, n, w):
+    """The graded workload at reduced order: column norms from 1 down to 1e-8."""
+    from paper_1008_0201_gb300 import inputs
+
+    G, J = inputs.config3_graded_complex(n=n, salt=1)
+    out = run(G, None, cuda_dev, block_w=w, precision="fp32")
+    assert out["status"] == 0, out["info"]
+    compare(G, J, out)
+
+
+def test_complex_errors(cuda_dev):
+    import torch
+
+    from paper_1008_0201_gb300 import binding
+
+    g = np.random.default_rng(5)
+    G = cgauss(g, 12, 12)
+    Gn = G.copy()
+    Gn[2, 3] = np.nan
+    assert run(Gn, None, cuda_dev, block_w=4)["status"] == binding.JAC_ENONFINITE
+    J = np.ones(12, dtype=np.int8)
+    J[4] = 3
+    with pytest.raises(binding.JacobiError) as e:
+        binding.jacobi_hsvd(torch.from_numpy(G).to(cuda_dev), torch.from_numpy(J).to(cuda_dev),
+                            binding.default_opts(block_w=4))
+    assert e.value.code == -6
