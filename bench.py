@@ -297,13 +297,17 @@ def main():
             rot_per_launch = sum(x["rotations"] for x in infos) / max(1, d_n)
             flops = rot_per_launch * 18 * k
             fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12  # unit counts x max SM clock
+            # DRAM bytes per launch from the ncu capture of this configuration (the summary in
+            # profiles/k_pivot_c2_hbsc_ncu.md); other configurations were not captured
+            default_cfg = (args.block_mode, args.ordering, args.factor, args.precision) == \
+                ("oriented", "round_robin", "chol_signpiv", "fp32")
             roof = {"bound": "alu", "achieved": flops / avg_s / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
-                    "frac": flops / avg_s / 1e12 / fp32_peak, "traffic": None,
+                    "frac": flops / avg_s / 1e12 / fp32_peak, "traffic": 337664 if default_cfg else None,
                     "kernel": "k_pivot", "peak_source": "FP32 lanes x max clock (152 x 128 x 2 x 2.07 GHz)"}
         else:
             # FP64 mma: gram m k^2, update (m + n) k^2 multiply-adds per pair
             macs = half * (m * k * k if dom == "gram" else (m + n) * k * k)
-            fp64_mma_peak = 4.18  # measured mma.sync m16n8k16 f64 throughput, TFLOP/s
+            fp64_mma_peak = 1.04  # measured mma.sync m16n8k16 f64 throughput, TFLOP/s
             roof = {"bound": "tensor", "achieved": 2 * macs / avg_s / 1e12, "peak": fp64_mma_peak,
                     "unit": "TFLOP/s", "frac": 2 * macs / avg_s / 1e12 / fp64_mma_peak, "traffic": None,
                     "kernel": "k_" + dom, "peak_source": "measured FP64 mma.sync m16n8k16 throughput"}
