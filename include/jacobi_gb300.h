@@ -120,6 +120,8 @@ typedef struct {
                                 J-orthogonalization */
   double sweep_max_scaled[64]; /* per sweep (first 64): max |a_ij| / sqrt(a_ii a_jj) seen */
   long long inner_sweeps;  /* inner sweeps summed over the transformed pivot blocks */
+  double sweep_ms[64];     /* per sweep (first 64): host wall time from its first launch to its
+                              completion, the precision switch included (single solves) */
 } jac_info;
 
 /* Fills *opts with the defaults: w = 32, round-robin, full block, sign-pivoted Cholesky,

@@ -34,12 +34,14 @@ class JacInfo(ctypes.Structure):
                 ("off_rel", ctypes.c_double), ("launches", ctypes.c_longlong), ("lowp_sweeps", ctypes.c_int),
                 ("global_ns_steps", ctypes.c_int), ("pivot_ns_steps", ctypes.c_longlong),
                 ("pivot_cycles", ctypes.c_longlong * 4), ("sweep_max_scaled", ctypes.c_double * 64),
-                ("inner_sweeps", ctypes.c_longlong)]
+                ("inner_sweeps", ctypes.c_longlong), ("sweep_ms", ctypes.c_double * 64)]
 
     def as_dict(self):
-        d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("pivot_cycles", "sweep_max_scaled")}
+        d = {f: getattr(self, f) for f, _ in self._fields_
+             if f not in ("pivot_cycles", "sweep_max_scaled", "sweep_ms")}
         d["pivot_cycles"] = list(self.pivot_cycles)
         d["sweep_max_scaled"] = list(self.sweep_max_scaled[: self.sweeps])
+        d["sweep_ms"] = list(self.sweep_ms[: self.sweeps])
         return d
 
 

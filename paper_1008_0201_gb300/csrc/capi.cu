@@ -6,6 +6,7 @@
 // every step of the ordering, then the sweep reduction.  The only values read back per sweep
 // are one small record (single solve) or the number of problems still active (batch).
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstddef>
 #include <cstdio>
@@ -96,14 +97,16 @@ struct ProfRun {
     if (!a || !b) return (size_t)-1;
     evs.push_back(a);
     evs.push_back(b);
-    cudaEventRecord(a, st);
+    // external: inside a stream capture the record becomes a graph node that records the event
+    // at every replay (a plain record would only order the capture)
+    cudaEventRecordWithFlags(a, st, cudaEventRecordExternal);
     marks.emplace_back(k, evs.size() - 2);
     return evs.size() - 2;
   }
   void post(size_t idx, cudaStream_t st) {
-    if (idx != (size_t)-1) cudaEventRecord(evs[idx + 1], st);
+    if (idx != (size_t)-1) cudaEventRecordWithFlags(evs[idx + 1], st, cudaEventRecordExternal);
   }
-  void finish() {  // after the stream has been synchronized
+  void accumulate() {  // after the stream has been synchronized; the events stay with this run
     if (evs.empty()) return;
     std::lock_guard<std::mutex> lk(g_prof_mutex);
     for (auto& mk : marks) {
@@ -111,11 +114,20 @@ struct ProfRun {
       if (cudaEventElapsedTime(&ms, evs[mk.second], evs[mk.second + 1]) == cudaSuccess && g_prof_mask) {
         g_prof_ms[mk.first] += ms;
         g_prof_n[mk.first] += 1;
+      } else {
+        cudaGetLastError();  // a timing failure must not surface as a later launch error
       }
     }
+  }
+  void release() {
+    std::lock_guard<std::mutex> lk(g_prof_mutex);
     for (auto e : evs) g_prof_pool.push_back(e);
     evs.clear();
     marks.clear();
+  }
+  void finish() {  // after the stream has been synchronized
+    accumulate();
+    release();
   }
 };
 
@@ -177,9 +189,12 @@ int compute_nb(int n, int w) {
   return nb;
 }
 
-int choose_cluster(int half, int mp) {
+// CTAs per pivot block of the Gram kernels (a cluster splitting the rows): the FP64 Gram is
+// bound by the FP64 mma rate and takes every SM it can (>= 16 rows per CTA); the FP32 Gram is
+// ~64x cheaper per row, so its CTAs keep >= 128 rows and the cluster reduction stays short.
+int choose_cluster(int half, int mp, int min_rows) {
   int cs = 1;
-  while (cs * 2 <= 16 && half * cs * 2 <= 2 * 152 && mp / (cs * 2) >= 16) cs *= 2;
+  while (cs * 2 <= 16 && half * cs * 2 <= 2 * 152 && mp / (cs * 2) >= min_rows) cs *= 2;
   return cs;
 }
 
@@ -266,12 +281,12 @@ void carve_problem(Arena& ar, const Plan& P, JacProb& d, JacIO& io, bool weights
 }
 
 // One launch of the three step kernels for every problem of a class array.
-int launch_step(JacProb* dprobs, int count, int km, int max_half, int gslabs, int tslabs, int CS, int s, bool lowp,
-                const PivotParams& pp, cudaStream_t st, ProfRun& prof, long long& launches) {
+int launch_step(JacProb* dprobs, int count, int km, int max_half, int gslabs, int tslabs, int CS, int CS32, int s,
+                bool lowp, const PivotParams& pp, cudaStream_t st, ProfRun& prof, long long& launches) {
   int r = 0;
   size_t pm = prof.pre(JAC_KERNEL_GRAM, st);
   if (lowp)
-    r = launch_cluster(k_gram32, dim3(max_half * CS, count), CS, 128, 0, st, (const JacProb*)dprobs, s, CS);
+    r = launch_cluster(k_gram32, dim3(max_half * CS32, count), CS32, 128, 0, st, (const JacProb*)dprobs, s, CS32);
   else
     r = launch_cluster(k_gram, dim3(max_half * CS, count), CS, 128, kGramSmem, st, (const JacProb*)dprobs, s, CS);
   prof.post(pm, st);
@@ -289,6 +304,53 @@ int launch_step(JacProb* dprobs, int count, int km, int max_half, int gslabs, in
   launches += 4;
   return cudaGetLastError() == cudaSuccess ? 0 : JAC_ECUDA;
 }
+
+// One sweep's launches recorded once as a CUDA graph and replayed every sweep with the same
+// parameters (the launches of a sweep differ only by the step index, which the graph holds).
+// Capture runs on a private stream of the device (the caller's stream may be the legacy default
+// stream, which cannot be captured); the graph is launched on the caller's stream.
+std::mutex g_capture_mutex;
+cudaStream_t g_capture_stream[64] = {};
+
+struct SweepGraph {
+  cudaGraphExec_t exec = nullptr;
+  long long launches = 0;  // kernels per replay
+  ProfRun prof;            // event pairs recorded by the graph (kernel timing on), read per replay
+  ~SweepGraph() {
+    if (exec) cudaGraphExecDestroy(exec);
+    prof.release();
+  }
+  // record(stream, launches&) issues the sweep's launches; returns 0 or a status
+  template <class Fn>
+  int build(Fn record) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return JAC_ECUDA;
+    std::lock_guard<std::mutex> lk(g_capture_mutex);
+    if (!g_capture_stream[dev] &&
+        cudaStreamCreateWithFlags(&g_capture_stream[dev], cudaStreamNonBlocking) != cudaSuccess)
+      return JAC_ECUDA;
+    cudaStream_t cs = g_capture_stream[dev];
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return JAC_ECUDA;
+    long long n = 0;
+    const int r = record(cs, n);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(cs, &g);
+    if (r || e != cudaSuccess || !g) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return r ? r : JAC_ECUDA;
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&exec, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+      exec = nullptr;
+      cudaGetLastError();
+      return JAC_ECUDA;
+    }
+    launches = n;
+    return 0;
+  }
+};
 
 struct ArgPos {  // 1-based positions of the arguments in the public signature
   int m, n, dtype, G, ldg, J, opts, lambda, U, ldu, V, ldv;
@@ -436,7 +498,7 @@ int solve_real(int m, int n, int dtype, void* Gv, int ldg, const int8_t* Jdev, c
     ++launches;
     ck(cudaGetLastError());
   }
-  const int CS = choose_cluster(P.half, P.mp);
+  const int CS = choose_cluster(P.half, P.mp, 16), CS32 = choose_cluster(P.half, P.mp, 128);
   const int gslabs = (P.mp + 63) / 64;
   const int tslabs = gslabs + (have_vw ? (P.np + 63) / 64 : 0);
   const int ew_blocks = std::min(1024, (int)(((size_t)P.mp * n + 255) / 256));
@@ -457,7 +519,16 @@ int solve_real(int m, int n, int dtype, void* Gv, int ldg, const int8_t* Jdev, c
   int last_steps = 0;
   ProfRun prof;
   prof.begin();
+  double sweep_ms_h[64] = {};
+  SweepGraph graphs[5];
+  bool use_graphs = !weights;
   for (int sw = 0; status == JAC_OK && n > 1 && sw < o.max_sweeps; ++sw) {
+    const auto t_sweep = std::chrono::steady_clock::now();
+    auto sweep_done = [&]() {
+      if (sw < 64)
+        sweep_ms_h[sw] =
+            std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_sweep).count();
+    };
     const bool low = (phase == 1 || phase == 4);
     PivotParams pp;
     pp.tol = (phase == 1) ? tau_lo : o.tol;
@@ -486,14 +557,33 @@ int solve_real(int m, int n, int dtype, void* Gv, int ldg, const int8_t* Jdev, c
         break;
       }
     }
-    for (int s = 0; s < nsteps && status == JAC_OK; ++s)
-      if (int r = launch_step(L.probs, 1, P.km, P.half, gslabs, tslabs, CS, s, low, pp, st, prof, launches))
-        status = r;
-    k_sweep_reduce<<<1, 256, 0, st>>>(L.probs, L.io, L.rec, 0, nullptr);
-    ++launches;
-    ck(cudaGetLastError());
+    auto record = [&](cudaStream_t ss, long long& nl, ProfRun& pr) -> int {
+      for (int s = 0; s < nsteps; ++s)
+        if (int r = launch_step(L.probs, 1, P.km, P.half, gslabs, tslabs, CS, CS32, s, low, pp, ss, pr, nl)) return r;
+      k_sweep_reduce<<<1, 256, 0, ss>>>(L.probs, L.io, L.rec, 0, nullptr);
+      ++nl;
+      return cudaGetLastError() == cudaSuccess ? 0 : JAC_ECUDA;
+    };
+    // graphs: one per precision phase, unless the ordering is re-planned every sweep
+    SweepGraph& sg = graphs[phase];
+    if (use_graphs && !sg.exec) {
+      sg.prof.begin();
+      if (sg.build([&](cudaStream_t ss, long long& nl) { return record(ss, nl, sg.prof); })) {
+        sg.prof.release();
+        use_graphs = false;
+      }
+    }
+    SweepGraph* replayed = nullptr;
+    if (use_graphs && sg.exec) {
+      if (cudaGraphLaunch(sg.exec, st) != cudaSuccess) status = JAC_ECUDA;
+      launches += sg.launches;
+      replayed = &sg;
+    } else if (int r = record(st, launches, prof)) {
+      status = r;
+    }
     ck(cudaMemcpyAsync(&hrec, L.rec, sizeof(SweepRecord), cudaMemcpyDeviceToHost, st));
     ck(cudaStreamSynchronize(st));
+    if (replayed) replayed->prof.accumulate();
     if (status != JAC_OK) break;
     if (info && sweeps < 64) info->sweep_max_scaled[sweeps] = hrec.max_scaled;
     ++sweeps;
@@ -518,10 +608,15 @@ int solve_real(int m, int n, int dtype, void* Gv, int ldg, const int8_t* Jdev, c
     }
     if (phase == 1) {
       ++lowp_sweeps;
-      // leave the FP32 phase when it has converged at tau_lo, when the off-norm stalls, when a
-      // block is singular in FP32, or when only the sweeps the polish needs are left
+      // leave the FP32 phase once the sweep has entered the quadratic regime (max scaled
+      // off-diagonal below 1e-2): the switch itself resets the off-norm to the accuracy of the
+      // FP32-accumulated V (~1e-4..1e-3 for the hyperbolic workload whatever the FP32 phase
+      // reached), so further FP32 sweeps buy nothing.  Also when it has converged at tau_lo,
+      // when the off-norm stalls, when a block is singular in FP32, or when only the sweeps the
+      // polish needs are left.
       const bool stalled = hrec.max_scaled < 1e-3 && hrec.max_scaled > 0.5 * prev_max;
-      const bool done = hrec.pivots_rotated == 0 || stalled || lowp_singular || sw + 4 >= o.max_sweeps;
+      const bool done = hrec.pivots_rotated == 0 || hrec.max_scaled < 1e-2 || stalled || lowp_singular ||
+                        sw + 4 >= o.max_sweeps;
       prev_max = hrec.max_scaled;
       if (done) {
         // V (FP32) -> FP64, J-unitary by Newton-Schulz, then G = G_in V
@@ -557,10 +652,13 @@ int solve_real(int m, int n, int dtype, void* Gv, int ldg, const int8_t* Jdev, c
                                                                         nullptr, hp.Gw, P.mp, 0, 0, 0, 0, 0);
         ++launches;
         ck(cudaGetLastError());
+        ck(cudaStreamSynchronize(st));
         phase = 3;
       }
+      sweep_done();
       continue;
     }
+    sweep_done();
     if (hrec.pivots_rotated == 0) {
       converged = 1;
       break;
@@ -584,6 +682,7 @@ int solve_real(int m, int n, int dtype, void* Gv, int ldg, const int8_t* Jdev, c
   prof.finish();
   if (info) {
     for (int u = sweeps; u < 64; ++u) info->sweep_max_scaled[u] = 0.0;
+    for (int u = 0; u < 64; ++u) info->sweep_ms[u] = (u < sweeps) ? sweep_ms_h[u] : 0.0;
     info->sweeps = sweeps;
     info->converged = converged;
     info->status = status;
@@ -683,12 +782,21 @@ int solve_complex(int m, int n, void* Gv, int ldg, const int8_t* Jdev, const jac
       status = solve_real((int)m2, (int)n2, JAC_R64, Gr2, (int)m2, Jr2, &o2, lam_r, nullptr, 0, Vr, (int)n2, info, st, ap,
                           want_v ? Vr2 : nullptr);
     if (info) {  // totals over both passes; the per-sweep maxima of pass 1, then of pass 2
-      double merged[64];
+      double merged[64], merged_ms[64];
       int t = 0;
-      for (int u = 0; u < info1.sweeps && u < 64 && t < 64; ++u) merged[t++] = info1.sweep_max_scaled[u];
-      for (int u = 0; u < info->sweeps && u < 64 && t < 64; ++u) merged[t++] = info->sweep_max_scaled[u];
-      while (t < 64) merged[t++] = 0.0;
-      for (int u = 0; u < 64; ++u) info->sweep_max_scaled[u] = merged[u];
+      for (int u = 0; u < info1.sweeps && u < 64 && t < 64; ++u, ++t) {
+        merged[t] = info1.sweep_max_scaled[u];
+        merged_ms[t] = info1.sweep_ms[u];
+      }
+      for (int u = 0; u < info->sweeps && u < 64 && t < 64; ++u, ++t) {
+        merged[t] = info->sweep_max_scaled[u];
+        merged_ms[t] = info->sweep_ms[u];
+      }
+      for (; t < 64; ++t) merged[t] = merged_ms[t] = 0.0;
+      for (int u = 0; u < 64; ++u) {
+        info->sweep_max_scaled[u] = merged[u];
+        info->sweep_ms[u] = merged_ms[u];
+      }
       info->sweeps += info1.sweeps;
       info->rotations += info1.rotations;
       info->pivots_rotated += info1.pivots_rotated;
@@ -924,19 +1032,40 @@ int solve_batched(int batch, const int* m, const int* n, int dtype, void* const*
   prof.begin();
   long long launches = 0;
   int sweeps = 0;
+  SweepGraph graph;  // every sweep of a batch has the same launches
+  bool use_graph = true;
   for (int sw = 0; status == JAC_OK && sw < o.max_sweeps; ++sw) {
-    ck(cudaMemsetAsync(d_remaining, 0, sizeof(int), st));
-    for (auto& c : cls) {
-      for (int s = 0; s < c.max_steps && status == JAC_OK; ++s)
-        if (int r = launch_step(c.probs, c.count, c.km, c.max_half, c.gslabs, c.tslabs, 1, s, fp32_only, pp, st, prof,
-                                launches))
-          status = r;
-      k_sweep_reduce<<<c.count, 256, 0, st>>>(c.probs, c.io, c.rec, 1, d_remaining);
-      ++launches;
+    auto record = [&](cudaStream_t ss, long long& nl, ProfRun& pr) -> int {
+      if (cudaMemsetAsync(d_remaining, 0, sizeof(int), ss) != cudaSuccess) return JAC_ECUDA;
+      for (auto& c : cls) {
+        for (int s = 0; s < c.max_steps; ++s)
+          if (int r = launch_step(c.probs, c.count, c.km, c.max_half, c.gslabs, c.tslabs, 1, 1, s, fp32_only, pp, ss,
+                                  pr, nl))
+            return r;
+        k_sweep_reduce<<<c.count, 256, 0, ss>>>(c.probs, c.io, c.rec, 1, d_remaining);
+        ++nl;
+      }
+      return cudaGetLastError() == cudaSuccess ? 0 : JAC_ECUDA;
+    };
+    if (use_graph && !graph.exec) {
+      graph.prof.begin();
+      if (graph.build([&](cudaStream_t ss, long long& nl) { return record(ss, nl, graph.prof); })) {
+        graph.prof.release();
+        use_graph = false;
+      }
+    }
+    bool replayed = false;
+    if (use_graph && graph.exec) {
+      if (cudaGraphLaunch(graph.exec, st) != cudaSuccess) status = JAC_ECUDA;
+      launches += graph.launches;
+      replayed = true;
+    } else if (int r = record(st, launches, prof)) {
+      status = r;
     }
     int remaining = 0;
     ck(cudaMemcpyAsync(&remaining, d_remaining, sizeof(int), cudaMemcpyDeviceToHost, st));
     ck(cudaStreamSynchronize(st));
+    if (replayed) graph.prof.accumulate();
     ++sweeps;
     if (remaining == 0) break;
   }

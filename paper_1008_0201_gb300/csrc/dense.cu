@@ -74,11 +74,13 @@ __global__ void __launch_bounds__(128) k_gram32(const JacProb* __restrict__ prob
   double* out = a.Ap + (size_t)pair * a.apld * a.apld;
   for (int e = e0 + tid; e < e1; e += 128) {
     const int i = e % k, j = e / k;
+    float part[16];  // all remote loads issued before the (fixed-order) sum
+#pragma unroll
+    for (int rk = 0; rk < 16; ++rk)
+      part[rk] = (rk < CS) ? cluster.map_shared_rank(&Cs[0][0], rk)[i * (JAC_KMAX + 1) + j] : 0.0f;
     float sum = 0.0f;
-    for (int rk = 0; rk < CS; ++rk) {
-      const float* rc = cluster.map_shared_rank(&Cs[0][0], rk);
-      sum += rc[i * (JAC_KMAX + 1) + j];
-    }
+#pragma unroll
+    for (int rk = 0; rk < 16; ++rk) sum += part[rk];
     out[j * a.apld + i] = (double)sum;
   }
   cluster.sync();

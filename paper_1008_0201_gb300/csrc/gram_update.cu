@@ -111,11 +111,12 @@ __global__ void __launch_bounds__(128) k_gram(const JacProb* __restrict__ probs,
   double* out = a.Ap + (size_t)pair * a.apld * a.apld;
   for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
     const int i = e % k, j = e / k;
+    double part[16];  // all remote loads issued before the (fixed-order) sum
+#pragma unroll
+    for (int rk = 0; rk < 16; ++rk) part[rk] = (rk < CS) ? cluster.map_shared_rank(Cs, rk)[i * GRAM_LDC + j] : 0.0;
     double sum = 0.0;
-    for (int rk = 0; rk < CS; ++rk) {
-      const double* rc = cluster.map_shared_rank(Cs, rk);
-      sum += rc[i * GRAM_LDC + j];
-    }
+#pragma unroll
+    for (int rk = 0; rk < 16; ++rk) sum += part[rk];
     out[j * a.apld + i] = sum;
   }
   cluster.sync();  // keep every partial alive until all remote reads are done
