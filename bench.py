@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--block-mode", default="oriented", choices=["full", "oriented"])
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-other-workloads", action="store_true")
     return ap.parse_args()
 
 
@@ -161,6 +162,101 @@ def reference_arm(args, rank, world):
             "e2e": {"value": val, "unit": "matrices/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
+
+
+def other_workloads(dev, steps=3):
+    """Secondary measurements of the other configurations (rank 0, after the headline).  Each is
+    the mean of `steps` solves timed with CUDA events on the current stream, inputs in HBM."""
+    import torch
+
+    from paper_1008_0201_gb300 import binding, inputs
+
+    stream = torch.cuda.current_stream(dev)
+    out = {}
+
+    def timed(fn, reps):
+        fn()  # warm-up
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    # C2 in plain FP64 (HFSC, per-cycle weight): the form the mixed-precision headline is compared to
+    G, J = inputs.config2_hyperbolic()
+    Gd = torch.from_numpy(G).to(dev)
+    Jd = torch.from_numpy(J).to(dev)
+    o64 = binding.default_opts(block_w=32, ordering="cycle_weight", block_mode="full", precision="fp64")
+    out["c2_hfsc_fp64_ms"] = timed(lambda: binding.jacobi_hsvd(Gd, Jd, o64), steps)
+    # C1: 64 x 64 positive definite, w = 8, modulus ordering
+    G1, _ = inputs.config1_pd()
+    G1d = torch.from_numpy(G1).to(dev)
+    o1 = binding.default_opts(block_w=8, ordering="modulus", block_mode="full", precision="fp64")
+    out["c1_pd64_fp64_ms"] = timed(lambda: binding.jacobi_eig_pd(G1d, o1), steps)
+    # C4: 10 000 problems of order 8..128, FP64 and FP32-only, against one call per problem
+    Gs, Js = inputs.config4_batched()
+    ns = np.array([x.shape[1] for x in Gs], dtype=np.int32)
+    offs = np.concatenate([[0], np.cumsum(ns.astype(np.int64) ** 2)])
+    joffs = np.concatenate([[0], np.cumsum(ns.astype(np.int64))])
+    G0 = torch.from_numpy(np.concatenate([np.asfortranarray(x).ravel(order="F") for x in Gs])).to(dev)
+    Jb = torch.from_numpy(np.concatenate(Js).astype(np.int8)).to(dev)
+    Gw = torch.empty_like(G0)
+    lam = torch.empty(int(joffs[-1]), dtype=torch.float64, device=dev)
+    Vb = torch.empty(int(offs[-1]), dtype=torch.float64, device=dev)
+    ptr = lambda t, o, es: (np.uint64(t.data_ptr()) + o[:-1].astype(np.uint64) * np.uint64(es)).astype(np.uint64)
+
+    def batched(prec):
+        ob = binding.default_opts(precision=prec, want_v=1)
+
+        def run():
+            Gw.copy_(G0)
+            binding.jacobi_eig_batched_raw(ns, ns, ptr(Gw, offs, 8), ns, ptr(Jb, joffs, 1), ob, ptr(lam, joffs, 8),
+                                           None, None, ptr(Vb, offs, 8), ns, stream.cuda_stream, want_info=False)
+        return run
+
+    ms64 = timed(batched("fp64"), 2)
+    ms32 = timed(batched("fp32_only"), 2)
+    sample = 200
+    oloop = binding.default_opts(block_w=16, ordering="round_robin", precision="fp64")
+    Gl = [torch.from_numpy(x).to(dev) for x in Gs[:sample]]
+    Jl = [torch.from_numpy(x).to(dev) for x in Js[:sample]]
+
+    def loop():
+        for a, b in zip(Gl, Jl):
+            binding.jacobi_hsvd(a, b, oloop, raise_on_error=False)
+    msl = timed(loop, 1)
+    out["c4_batched_fp64"] = {"ms": ms64, "matrices_per_s": len(Gs) * 1e3 / ms64}
+    out["c4_batched_fp32_only"] = {"ms": ms32, "matrices_per_s": len(Gs) * 1e3 / ms32}
+    out["c4_one_call_per_problem_fp64"] = {"sample": sample, "matrices_per_s": sample * 1e3 / msl}
+    # C5: forward (batched, 256 problems of order 256) and the backward kernel
+    Gc, w, C = inputs.config5_backward()
+    H = np.einsum("bij,bkj->bik", Gc, Gc) + 0.1 * np.eye(Gc.shape[1])
+    L = torch.from_numpy(np.linalg.cholesky(H)).to(dev)
+    o5 = binding.default_opts(want_v=0)
+    res = {}
+
+    def fwd():
+        res["o"] = binding.jacobi_eig_batched_uniform(L, None, o5)
+    ms_f = timed(fwd, 2)
+    lamr, Ur = res["o"]["lam"], res["o"]["U"]
+    wt = torch.from_numpy(w).to(dev).expand_as(lamr).contiguous()
+    Ct = torch.from_numpy(C).to(dev)
+    Ub = torch.zeros_like(Ur)
+    Ub[..., :8] = 2.0 * Ct @ (Ct.T @ Ur[..., :8])
+    ms_b = timed(lambda: binding.jacobi_eig_backward(lamr, Ur, wt, Ub), 3)
+    n5 = Gc.shape[1]
+    out["c5_forward"] = {"ms": ms_f, "matrices_per_s": Gc.shape[0] * 1e3 / ms_f}
+    out["c5_backward"] = {"ms": ms_b, "tflops_fp64": 3 * 2 * Gc.shape[0] * n5 ** 3 / (ms_b * 1e-3) / 1e12}
+    # C3 at reduced order (the full n = 4096 takes ~30 s): graded complex, mixed precision
+    G3, _ = inputs.config3_graded_complex(n=1024)
+    G3d = torch.from_numpy(G3).to(dev)
+    o3 = binding.default_opts(block_w=32, ordering="round_robin", block_mode="oriented", precision="fp32")
+    out["c3_graded_complex_n1024_ms"] = timed(lambda: binding.jacobi_eig_pd(G3d, o3), 1)
+    return out
 
 
 def main():
@@ -348,6 +444,8 @@ def main():
         }
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline()
+        if not args.no_other_workloads and world == 1:
+            line["other_workloads"] = other_workloads(dev)
         print(json.dumps(line))
     if dist:
         dist.barrier()
