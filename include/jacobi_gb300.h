@@ -75,8 +75,10 @@ enum jac_block_mode {
 
 /* Factorization of the pivot block A_P = G_P^* G_P (Sec. 3.2). */
 enum jac_factor {
-  JAC_FACTOR_CHOL = 0,        /* unpivoted Cholesky (HF) */
-  JAC_FACTOR_CHOL_SIGNPIV = 2 /* J_P-sign-pivoted Cholesky, Algorithm 3.3 (HFSC) */
+  JAC_FACTOR_CHOL = 0,         /* unpivoted Cholesky (HF) */
+  JAC_FACTOR_CHOL_DIAGPIV = 1, /* Cholesky with diagonal pivoting over the whole block (HFC, Sec. 3.2);
+                                  J_P follows the pivot order */
+  JAC_FACTOR_CHOL_SIGNPIV = 2  /* J_P-sign-pivoted Cholesky, Algorithm 3.3 (HFSC) */
 };
 
 /* Arithmetic of the sweeps (FP64 and FP32 return FP64-accurate results). */

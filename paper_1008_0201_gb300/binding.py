@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libjacobi_gb300.so")
 JAC_OK, JAC_ENOTCONV, JAC_ENOTPD, JAC_ENONFINITE, JAC_ECUDA, JAC_ENOMEM, JAC_EINTERNAL = range(7)
 JAC_R64, JAC_C128 = 0, 1
 ORDER = {"modulus": 0, "modulus_mod": 1, "round_robin": 2, "cycle_weight": 3}
-FACTOR = {"chol": 0, "chol_signpiv": 2}
+FACTOR = {"chol": 0, "chol_diagpiv": 1, "chol_signpiv": 2}
 PRECISION = {"fp64": 0, "fp32": 1, "fp32_only": 2}
 BLOCK_MODE = {"full": 0, "oriented": 1}
 

@@ -173,7 +173,8 @@ int check_opts(const jac_opts& o, int argpos, bool batch) {
   if (o.ordering < 0 || o.ordering > 3) return -argpos;
   if (batch && o.ordering == JAC_ORDER_CYCLE_WEIGHT) return -argpos;
   if (o.block_mode != JAC_BLOCK_FULL && o.block_mode != JAC_BLOCK_ORIENTED) return -argpos;
-  if (o.factor != JAC_FACTOR_CHOL && o.factor != JAC_FACTOR_CHOL_SIGNPIV) return -argpos;
+  if (o.factor != JAC_FACTOR_CHOL && o.factor != JAC_FACTOR_CHOL_DIAGPIV && o.factor != JAC_FACTOR_CHOL_SIGNPIV)
+    return -argpos;
   if (o.precision < JAC_PREC_FP64 || o.precision > JAC_PREC_FP32_ONLY) return -argpos;
   if (batch && o.precision == JAC_PREC_FP32) return -argpos;
   if (o.max_sweeps < 1) return -argpos;

@@ -3,9 +3,10 @@
 // For the pair (p, q) of a step, with X = [G_p G_q] (m x k) and A_P = X^* X (from the gram
 // kernel):
 //  1. convergence statistics of A_P: rotate the block iff some |a_ij| > tol sqrt(a_ii a_jj);
-//  2. the Cholesky factor P^T A_P P = R^* R (Sec. 3.2), unpivoted (HF) or J_P-sign-pivoted
-//     (Algorithm 3.3, HFSC: diagonal pivoting inside the J = +1 part, then inside the Schur
-//     complement of the J = -1 part, whose columns are then taken in reverse order);
+//  2. the Cholesky factor P^T A_P P = R^* R (Sec. 3.2), unpivoted (HF), with diagonal pivoting
+//     over the whole block (HFC) or J_P-sign-pivoted (Algorithm 3.3, HFSC: diagonal pivoting
+//     inside the J = +1 part, then inside the Schur complement of the J = -1 part, whose columns
+//     are then taken in reverse order);
 //  3. the pointwise one-sided Jacobi on the columns of R with respect to J_P (Sec. 2.1, the
 //     "one-sided manner" of Sec. 2.2), trigonometric rotations (Eq. (2.1)) for equal signs and
 //     hyperbolic ones otherwise, with the tanh = +-1 guard of Sec. 3.2, repeated until an inner
@@ -235,7 +236,7 @@ __global__ void __launch_bounds__((KM / 2) * LPP, 1)
   int npos = 0;
   for (int c = 0; c < k; ++c) npos += (sm.jloc[c] > 0) ? 1 : 0;  // J sorted: + block first
   __syncthreads();
-  const bool signpiv = (pp.factor == 2);
+  const bool signpiv = (pp.factor == 2), diagpiv = (pp.factor == 1);
   // Right-looking Cholesky of I + E with diagonal pivoting inside the sign groups, on unpermuted
   // storage: the trailing entry (a, b), a < b (local indices), stays at S[b * LDS + a]; the pivot
   // of step i is perm[i]; row i of R~ - I is kept by column index in Fr; the shifted Schur
@@ -265,12 +266,13 @@ __global__ void __launch_bounds__((KM / 2) * LPP, 1)
     const float* dg = sm.dg[i & 1];
     float* dgn = sm.dg[(i + 1) & 1];
     int p = i;
-    if (signpiv) {
-      // the largest unscaled Schur diagonal d_j^2 (1 + s_jj) in the sign group of step i
+    if (signpiv || diagpiv) {
+      // the largest unscaled Schur diagonal d_j^2 (1 + s_jj): in the sign group of step i
+      // (sign pivoting, Algorithm 3.3) or among all remaining columns (diagonal pivoting, HFC)
       // key: the value's bits above the low 6 (order-preserving for v >= 0) and 63 - j, so one
       // warp max-reduction yields the largest value, ties to the smaller index; every warp
       // computes the same key
-      const int lo = (i < npos) ? 0 : npos, hi = (i < npos) ? npos : k;
+      const int lo = (signpiv && i >= npos) ? npos : 0, hi = (signpiv && i < npos) ? npos : k;
       unsigned key = 0u;
       for (int j = lo + lane; j < hi; j += 32) {
         if ((done >> j) & 1ull) continue;
@@ -361,7 +363,17 @@ __global__ void __launch_bounds__((KM / 2) * LPP, 1)
   if (tid < k) {
     sm.dd[tid] = d_new;
     sm.jphys[tid] = j_new;
-    sm.lpos[tid] = (signpiv && tid >= npos) ? (k - 1 - (tid - npos)) : tid;
+    if (diagpiv) {
+      // diagonal pivoting mixes the signs: the output order puts the pivot-order columns back
+      // on positions of their own sign (positives, then negatives, each in pivot order), so
+      // that V_P^* J_P V_P = J_P in the block's local order (the reordering of HFC)
+      const bool pos = j_new > 0;
+      int rank = 0;
+      for (int c = 0; c < tid; ++c) rank += ((sm.jloc[sm.perm[c]] > 0) == pos) ? 1 : 0;
+      sm.lpos[pos ? rank : npos + rank] = tid;
+    } else {
+      sm.lpos[tid] = (signpiv && tid >= npos) ? (k - 1 - (tid - npos)) : tid;
+    }
     if (cross_only) {
       const bool in_p = sm.perm[tid] < wp;
       int rank = 0;

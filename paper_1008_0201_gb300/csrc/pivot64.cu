@@ -5,9 +5,9 @@
 //
 // The computation is the one of Sec. 3.2 / Algorithm 3.4 for one block, as the paper runs it:
 //  1. the scaled Gram A~ = D^-1 A_P D^-1 (D = diag(sqrt(a_ii))), factored P^T A~ P = R~^T R~ by
-//     Cholesky, unpivoted (HF) or J_P-sign-pivoted (Algorithm 3.3: diagonal pivoting inside the
-//     J = +1 part, then inside the Schur complement of the J = -1 part, on the unscaled
-//     diagonal d_j^2 s_jj);
+//     Cholesky, unpivoted (HF), diagonally pivoted (HFC) or J_P-sign-pivoted (Algorithm 3.3:
+//     diagonal pivoting inside the J = +1 part, then inside the Schur complement of the J = -1
+//     part), pivoting on the unscaled diagonal d_j^2 s_jj;
 //  2. R = R~ D (so R^T R = P^T A_P P) and the pointwise one-sided Jacobi on its columns w.r.t.
 //     J_P: trigonometric rotations (Eq. (2.1)) for equal signs, hyperbolic ones otherwise with
 //     the |tanh| < 1 guard of Sec. 3.2; the columns of the J = -1 part are taken in reverse
@@ -78,12 +78,12 @@ __global__ void __launch_bounds__(KM * 16, 1) k_pivot64(const JacProb* __restric
   for (int c = 0; c < k; ++c) npos += (sm.jloc[c] > 0) ? 1 : 0;  // J sorted: + part first
   if (tid < k) sm.jphys[tid] = sm.jloc[tid];
   __syncthreads();
-  const bool signpiv = (pp.factor == 2);
+  const bool signpiv = (pp.factor == 2), diagpiv = (pp.factor == 1);
   const int cx = tid % KM, cy = tid / KM;
   for (int i = 0; i < k; ++i) {
-    if (signpiv) {
+    if (signpiv || diagpiv) {
       if (warp == 0) {
-        const int hi = (i < npos) ? npos : k;
+        const int hi = (signpiv && i < npos) ? npos : k;
         double best = -1.0;
         int bj = i;
         for (int j = i + lane; j < hi; j += 32) {
@@ -166,7 +166,16 @@ __global__ void __launch_bounds__(KM * 16, 1) k_pivot64(const JacProb* __restric
     const int rr = e % k, c = e / k;
     if (rr <= c) sm.R[c * LD + rr] *= sm.dd[c];
   }
-  if (tid < k) sm.lpos[tid] = (signpiv && tid >= npos) ? (k - 1 - (tid - npos)) : tid;
+  if (tid < k) {
+    if (diagpiv) {  // positions of the own sign, as in the FP32 kernel (HFC reordering)
+      const bool pos = sm.jphys[tid] > 0;
+      int rank = 0;
+      for (int c = 0; c < tid; ++c) rank += ((sm.jphys[c] > 0) == pos) ? 1 : 0;
+      sm.lpos[pos ? rank : npos + rank] = tid;
+    } else {
+      sm.lpos[tid] = (signpiv && tid >= npos) ? (k - 1 - (tid - npos)) : tid;
+    }
+  }
   __syncthreads();
   const long long t_chol = clock64();
 

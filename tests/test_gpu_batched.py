@@ -141,3 +141,33 @@ def test_batched_argument_errors(cuda_dev):
     assert e.value.code == -3
     outs, rc = binding.jacobi_eig_batched([], None, binding.default_opts())
     assert outs == [] and rc == 0
+
+
+def test_batched_full_size_sampled(cuda_dev):
+    """The batched workload at full size (10 000 problems of order 8..128, FP64): every problem
+    converges, and 24 sampled problems match the oracle to the single-solve tolerances."""
+    import torch
+
+    from paper_1008_0201_gb300 import binding, inputs
+
+    Gs, Js = inputs.config4_batched()
+    ns = np.array([G.shape[1] for G in Gs], dtype=np.int32)
+    offs = np.concatenate([[0], np.cumsum(ns.astype(np.int64) ** 2)])
+    joffs = np.concatenate([[0], np.cumsum(ns.astype(np.int64))])
+    Gw = torch.from_numpy(np.concatenate([np.asfortranarray(G).ravel(order="F") for G in Gs])).to(cuda_dev)
+    Jd = torch.from_numpy(np.concatenate(Js).astype(np.int8)).to(cuda_dev)
+    lam = torch.empty(int(joffs[-1]), dtype=torch.float64, device=cuda_dev)
+    V = torch.empty(int(offs[-1]), dtype=torch.float64, device=cuda_dev)
+    ptr = lambda t, o, es: (np.uint64(t.data_ptr()) + o[:-1].astype(np.uint64) * np.uint64(es)).astype(np.uint64)
+    rc, infos = binding.jacobi_eig_batched_raw(ns, ns, ptr(Gw, offs, 8), ns, ptr(Jd, joffs, 1),
+                                               binding.default_opts(precision="fp64"), ptr(lam, joffs, 8), None,
+                                               None, ptr(V, offs, 8), ns, torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    assert rc == 0
+    assert all(infos[i].status == 0 for i in range(len(Gs)))
+    lam_h, G_h, V_h = lam.cpu().numpy(), Gw.cpu().numpy(), V.cpu().numpy()
+    for i in np.random.default_rng(4).choice(len(Gs), size=24, replace=False):
+        n = int(ns[i])
+        out = dict(lam=lam_h[joffs[i]:joffs[i + 1]], G=G_h[offs[i]:offs[i + 1]].reshape((n, n), order="F"),
+                   V=V_h[offs[i]:offs[i + 1]].reshape((n, n), order="F"), U=None)
+        compare(Gs[i], Js[i], out)

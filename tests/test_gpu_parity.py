@@ -26,7 +26,7 @@ def run(G, J, dev, **kw):
 
 
 @pytest.mark.parametrize("ordering", ["modulus", "modulus_mod", "round_robin", "cycle_weight"])
-@pytest.mark.parametrize("factor", ["chol", "chol_signpiv"])
+@pytest.mark.parametrize("factor", ["chol", "chol_diagpiv", "chol_signpiv"])
 def test_config1_pd_64(cuda_dev, ordering, factor):
     from paper_1008_0201_gb300 import inputs
 
@@ -37,7 +37,7 @@ def test_config1_pd_64(cuda_dev, ordering, factor):
 
 
 @pytest.mark.parametrize("ordering", ["round_robin", "cycle_weight", "modulus"])
-@pytest.mark.parametrize("factor", ["chol", "chol_signpiv"])
+@pytest.mark.parametrize("factor", ["chol", "chol_diagpiv", "chol_signpiv"])
 def test_config2_hyperbolic_512(cuda_dev, ordering, factor):
     from paper_1008_0201_gb300 import inputs
 
