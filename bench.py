@@ -218,8 +218,15 @@ def other_workloads(dev, steps=3):
                                            None, None, ptr(Vb, offs, 8), ns, stream.cuda_stream, want_info=False)
         return run
 
+    ms64_default = timed(batched("fp64"), 2)
+    # the library's width autotuner, per precision (about a second each)
+    rules64 = binding.jacobi_autotune_batched(count=256, precision="fp64", device=dev)
     ms64 = timed(batched("fp64"), 2)
+    rules32 = binding.jacobi_autotune_batched(count=256, precision="fp32_only", device=dev)
     ms32 = timed(batched("fp32_only"), 2)
+    binding.jacobi_autotune_batched(count=0, device=dev)
+    show = lambda r: {"%d-%d" % (lo, hi): int(r[lo]) for lo, hi in ((8, 16), (17, 32), (33, 48), (49, 64),
+                                                                      (65, 96), (97, 128))}
     sample = 200
     oloop = binding.default_opts(block_w=16, ordering="round_robin", precision="fp64")
     Gl = [torch.from_numpy(x).to(dev) for x in Gs[:sample]]
@@ -229,8 +236,9 @@ def other_workloads(dev, steps=3):
         for a, b in zip(Gl, Jl):
             binding.jacobi_hsvd(a, b, oloop, raise_on_error=False)
     msl = timed(loop, 1)
-    out["c4_batched_fp64"] = {"ms": ms64, "matrices_per_s": len(Gs) * 1e3 / ms64}
-    out["c4_batched_fp32_only"] = {"ms": ms32, "matrices_per_s": len(Gs) * 1e3 / ms32}
+    out["c4_batched_fp64"] = {"ms": ms64, "matrices_per_s": len(Gs) * 1e3 / ms64, "width_rules": show(rules64),
+                              "untuned_ms": ms64_default}
+    out["c4_batched_fp32_only"] = {"ms": ms32, "matrices_per_s": len(Gs) * 1e3 / ms32, "width_rules": show(rules32)}
     out["c4_one_call_per_problem_fp64"] = {"sample": sample, "matrices_per_s": sample * 1e3 / msl}
     # C5: forward (batched, 256 problems of order 256) and the backward kernel
     Gc, w, C = inputs.config5_backward()

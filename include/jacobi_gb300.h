@@ -239,6 +239,23 @@ int jacobi_eig_backward(int batch, int n, const double* lambda, long long s_lam,
                         long long s_gb, jac_stream_t stream);
 
 /*
+ * jacobi_autotune_batched -- measures, on the current device, which block width makes
+ * jacobi_eig_batched fastest for each size class of orders 8..128 (no counterpart in the paper;
+ * Sec. 3 leaves the block width free).  For each class (8-16, 17-32, 33-48, 49-64, 65-96,
+ * 97-128) it solves `count` synthetic problems (orders spread over the class, uniform entries,
+ * every third sign -1) once per candidate rule and keeps the fastest.  The candidates are
+ * one pivot block for the whole problem (rule 0, n <= 64) and fixed widths 8, 16 or 32.
+ * jacobi_eig_batched uses the measured rules on this device from then on.
+ *  1 count       problems per class, 1..4096; 0 restores the default widths on this device
+ *  2 precision   JAC_PREC_FP64 or JAC_PREC_FP32_ONLY (the arithmetic to tune for)
+ *  3 rules       host int[129] or NULL: the rule chosen for each order n (-1 outside 8..128)
+ *  4 stream
+ * Returns 0, a negative argument position, JAC_ENOMEM or JAC_ECUDA (the defaults then stay).
+ * Blocks the host; allocates its inputs with cudaMallocAsync.
+ */
+int jacobi_autotune_batched(int count, int precision, int* rules, jac_stream_t stream);
+
+/*
  * jacobi_sched_pairs -- the device scheduler on its own (Sec. 2.4), for inspection and tests.
  * Writes the block pairs of every step of one cycle for nb blocks (nb even, 2 <= nb <= 4096).
  *  1 nb

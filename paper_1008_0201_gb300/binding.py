@@ -56,7 +56,7 @@ _lib = None
 
 EXPORTS = ("jacobi_default_opts", "jacobi_status_string", "jacobi_version", "jacobi_hsvd", "jacobi_eig_pd",
            "jacobi_sched_pairs", "jacobi_profile_begin", "jacobi_profile_read", "jacobi_profile_end",
-           "jacobi_sched_pairs_noalloc", "jacobi_eig_batched", "jacobi_eig_backward")
+           "jacobi_sched_pairs_noalloc", "jacobi_eig_batched", "jacobi_eig_backward", "jacobi_autotune_batched")
 KERNEL = {"gram": 0, "pivot": 1, "update": 2}
 
 
@@ -84,6 +84,8 @@ def load_library(path=LIB_PATH):
     lib.jacobi_sched_pairs.restype = I
     lib.jacobi_eig_batched.argtypes = [I, P, P, I, P, P, P, ctypes.POINTER(JacOpts), P, P, P, P, P, P, P]
     lib.jacobi_eig_batched.restype = I
+    lib.jacobi_autotune_batched.argtypes = [I, I, P, P]
+    lib.jacobi_autotune_batched.restype = I
     L = ctypes.c_longlong
     lib.jacobi_eig_backward.argtypes = [I, I, P, L, P, I, L, P, L, P, I, L, D, P, I, L, P, I, L, P, L, P, I, L, P]
     lib.jacobi_eig_backward.restype = I
@@ -265,6 +267,22 @@ def jacobi_eig_batched(Gs, Js=None, opts=None, want_u=False, raise_on_error=True
         outs.append(dict(lam=lams[i], G=Gts[i].t(), U=Uts[i].t() if Uts is not None else None,
                          V=Vts[i].t() if Vts is not None else None, info=infos[i].as_dict()))
     return outs, rc
+
+
+def jacobi_autotune_batched(count=64, precision="fp64", device="cuda"):
+    """Measure and install the fastest block-width rule per size class for jacobi_eig_batched on
+    `device`; count=0 restores the defaults.  Returns the rule per order n (index 0..128)."""
+    import numpy as np
+
+    lib = load_library()
+    dev = torch.device(device)
+    rules = np.full(129, -1, dtype=np.int32)
+    with torch.cuda.device(dev):
+        rc = lib.jacobi_autotune_batched(int(count), PRECISION.get(precision, precision),
+                                         ctypes.c_void_p(rules.ctypes.data), _stream(dev))
+    if rc != JAC_OK:
+        raise JacobiError(rc, status_string(rc))
+    return rules
 
 
 def jacobi_eig_batched_uniform(G, J=None, opts=None, want_u=True, raise_on_error=True):

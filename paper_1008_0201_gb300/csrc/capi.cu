@@ -54,6 +54,7 @@ __global__ void k_realify(int m, int n, const double2* G, int ldg, const int8_t*
 __global__ void k_complexify(int m, int n, const double* Gr, const double* lam_r, const double* Vr, double2* G, int ldg,
                              double* lambda, double2* U, int ldu, double2* V, int ldv, unsigned* bad);
 __global__ void k_restructure(int h, int n, const double* in, double* out, const double* lam, int8_t* Jout);
+__global__ void k_fill_uniform(double* x, long long n, unsigned long long seed);
 }  // namespace jac
 
 using namespace jac;
@@ -216,10 +217,27 @@ int launch_cluster(Kern kern, dim3 grid, int CS, int threads, size_t smem, cudaS
   return cudaLaunchKernelEx(&cfg, kern, args...) == cudaSuccess ? 0 : JAC_ECUDA;
 }
 
-// Block width of one problem of a batch, by size class: the whole problem is one pivot block up
-// to n = 64 (nb = 2, one step per sweep, KM = 32 while n <= 32), blocks of 32 columns above
-// (nb = 4, three round-robin steps of two pivot blocks).
-int batch_width(int n) { return n <= 64 ? (n + 1) / 2 : 32; }
+// Block width of one problem of a batch, by size class.  Width rules: 0 = the whole problem is
+// one pivot block (w = ceil(n/2), one step per sweep; needs n <= 64), else a fixed width w.
+// Default: one block up to n = 64 (KM = 32 while n <= 32), blocks of 32 columns above (nb = 4,
+// three round-robin steps of two pivot blocks).  jacobi_autotune_batched replaces the default
+// per size class with the fastest rule it measures on the device.
+std::mutex g_tune_mutex;
+int g_tuned_rule[64][129];  // per device and order: -1 untuned, else a width rule
+bool g_tune_init = false;
+
+int width_of_rule(int rule, int n) { return rule == 0 ? (n + 1) / 2 : std::min(rule, (n + 1) / 2); }
+
+int batch_width(int n) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mutex);
+    if (g_tune_init && dev >= 0 && dev < 64 && n >= 0 && n <= 128 && g_tuned_rule[dev][n] >= 0)
+      return width_of_rule(g_tuned_rule[dev][n], n);
+  }
+  return n <= 64 ? (n + 1) / 2 : 32;
+}
 
 // Per-problem plan: sizes of its pieces.
 struct Plan {
@@ -1190,6 +1208,120 @@ int jacobi_eig_batched(int batch, const int* m, const int* n, int dtype, void* c
                        const int8_t* const* J, const jac_opts* opts, double* const* lambda, void* const* U,
                        const int* ldu, void* const* V, const int* ldv, jac_info* info, jac_stream_t stream) {
   return solve_batched(batch, m, n, dtype, G, ldg, J, opts, lambda, U, ldu, V, ldv, info, (cudaStream_t)stream);
+}
+
+int jacobi_autotune_batched(int count, int precision, int* rules, jac_stream_t stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return JAC_ECUDA;
+  if (count == 0) {  // back to the default widths on this device
+    std::lock_guard<std::mutex> lk(g_tune_mutex);
+    if (g_tune_init)
+      for (int n = 0; n <= 128; ++n) g_tuned_rule[dev][n] = -1;
+    if (rules)
+      for (int n = 0; n <= 128; ++n) rules[n] = -1;
+    return JAC_OK;
+  }
+  if (count < 1 || count > 4096) return -1;
+  if (precision != JAC_PREC_FP64 && precision != JAC_PREC_FP32_ONLY) return -2;
+  // size classes and the width rules tried in each (rule 0: one pivot block)
+  struct Cls {
+    int lo, hi;
+    int rules[3];
+  };
+  const Cls classes[] = {{8, 16, {0, 8, -1}},      {17, 32, {0, 8, -1}},      {33, 48, {0, 16, 8}},
+                         {49, 64, {0, 16, 32}},    {65, 96, {32, 16, -1}},    {97, 128, {32, 16, -1}}};
+  int best_rule[129];
+  for (int n = 0; n <= 128; ++n) best_rule[n] = -1;
+  jac_opts o;
+  jacobi_default_opts(&o);
+  o.precision = precision;
+  o.want_v = 1;
+  std::vector<int> ms(count), ns(count), ld(count);
+  std::vector<long long> offs(count + 1), joffs(count + 1);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return JAC_ECUDA;
+  int status = JAC_OK;
+  unsigned long long seed = 0x5EED5EEDull;
+  for (const Cls& c : classes) {
+    // problems of the class: orders spread evenly over [lo, hi], square, uniform entries, J with
+    // every third sign -1
+    offs[0] = joffs[0] = 0;
+    for (int b = 0; b < count; ++b) {
+      ns[b] = ms[b] = ld[b] = c.lo + (int)(((long long)b * (c.hi - c.lo + 1)) / count);
+      offs[b + 1] = offs[b] + (long long)ns[b] * ns[b];
+      joffs[b + 1] = joffs[b] + ns[b];
+    }
+    std::vector<int8_t> hJ((size_t)joffs[count]);
+    for (long long i = 0; i < joffs[count]; ++i) hJ[(size_t)i] = (i % 3 == 2) ? -1 : 1;
+    void* base = nullptr;
+    const size_t bytes = sizeof(double) * (3 * (size_t)offs[count] + (size_t)joffs[count]) + (size_t)joffs[count] + 256;
+    if (cudaMallocAsync(&base, bytes, st) != cudaSuccess) {
+      cudaGetLastError();
+      status = JAC_ENOMEM;
+      break;
+    }
+    double* G0 = static_cast<double*>(base);
+    double* Gw = G0 + offs[count];
+    double* Vb = Gw + offs[count];
+    double* lam = Vb + offs[count];
+    int8_t* Jb = reinterpret_cast<int8_t*>(lam + joffs[count]);
+    k_fill_uniform<<<1024, 256, 0, st>>>(G0, offs[count], seed++);
+    cudaMemcpyAsync(Jb, hJ.data(), hJ.size(), cudaMemcpyHostToDevice, st);
+    std::vector<void*> pG(count), pV(count);
+    std::vector<double*> pl(count);
+    std::vector<const int8_t*> pJ(count);
+    for (int b = 0; b < count; ++b) {
+      pG[b] = Gw + offs[b];
+      pV[b] = Vb + offs[b];
+      pl[b] = lam + joffs[b];
+      pJ[b] = Jb + joffs[b];
+    }
+    float best_ms = 1e30f;
+    int best = -1;
+    for (int r : c.rules) {
+      if (r < 0) continue;
+      if (r == 0 && c.hi > 64) continue;
+      {
+        std::lock_guard<std::mutex> lk(g_tune_mutex);
+        if (!g_tune_init) {
+          for (int d = 0; d < 64; ++d)
+            for (int n = 0; n <= 128; ++n) g_tuned_rule[d][n] = -1;
+          g_tune_init = true;
+        }
+        for (int n = c.lo; n <= c.hi; ++n) g_tuned_rule[dev][n] = r;  // candidate in force
+      }
+      float t = 0.0f;
+      for (int rep = 0; rep < 2 && status == JAC_OK; ++rep) {  // first run warms up
+        cudaMemcpyAsync(Gw, G0, sizeof(double) * offs[count], cudaMemcpyDeviceToDevice, st);
+        cudaEventRecord(e0, st);
+        const int rc = solve_batched(count, ms.data(), ns.data(), JAC_R64, pG.data(), ld.data(), pJ.data(), &o,
+                                     pl.data(), nullptr, nullptr, pV.data(), ld.data(), nullptr, st);
+        cudaEventRecord(e1, st);
+        if (rc < 0 || rc == JAC_ECUDA || rc == JAC_ENOMEM) status = (rc < 0) ? JAC_EINTERNAL : rc;
+        if (cudaEventSynchronize(e1) != cudaSuccess) status = JAC_ECUDA;
+        cudaEventElapsedTime(&t, e0, e1);
+      }
+      if (status != JAC_OK) break;
+      if (t < best_ms) {
+        best_ms = t;
+        best = r;
+      }
+    }
+    cudaFreeAsync(base, st);
+    cudaStreamSynchronize(st);
+    if (status != JAC_OK) break;
+    for (int n = c.lo; n <= c.hi; ++n) best_rule[n] = best;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mutex);
+    for (int n = 0; n <= 128; ++n) g_tuned_rule[dev][n] = (status == JAC_OK) ? best_rule[n] : -1;
+  }
+  if (rules)
+    for (int n = 0; n <= 128; ++n) rules[n] = (status == JAC_OK) ? best_rule[n] : -1;
+  return status;
 }
 
 int jacobi_sched_pairs(int nb, int ordering, const double* weights, int* pairs, int* counts, int max_steps,

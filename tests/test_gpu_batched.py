@@ -171,3 +171,23 @@ def test_batched_full_size_sampled(cuda_dev):
         out = dict(lam=lam_h[joffs[i]:joffs[i + 1]], G=G_h[offs[i]:offs[i + 1]].reshape((n, n), order="F"),
                    V=V_h[offs[i]:offs[i + 1]].reshape((n, n), order="F"), U=None)
         compare(Gs[i], Js[i], out)
+
+
+def test_batched_autotune(cuda_dev):
+    """The width autotuner installs one measured rule per size class; batches solved under the
+    tuned widths still match the oracle; count = 0 restores the defaults."""
+    from paper_1008_0201_gb300 import binding
+
+    rules = binding.jacobi_autotune_batched(count=48, precision="fp64", device=cuda_dev)
+    try:
+        for lo, hi, allowed in ((8, 16, {0, 8}), (17, 32, {0, 8}), (33, 48, {0, 16, 8}), (49, 64, {0, 16, 32}),
+                                (65, 96, {32, 16}), (97, 128, {32, 16})):
+            assert len(set(rules[lo:hi + 1])) == 1 and rules[lo] in allowed, (lo, hi, rules[lo:hi + 1])
+        assert np.all(rules[:8] == -1)
+        Gs, Js = small_batch(16, salt=21)
+        outs, rc = run_batched(Gs, Js, cuda_dev)
+        assert rc == 0
+        check_all(Gs, Js, outs)
+    finally:
+        reset = binding.jacobi_autotune_batched(count=0, device=cuda_dev)
+    assert np.all(reset == -1)
