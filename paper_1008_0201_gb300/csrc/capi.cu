@@ -193,7 +193,8 @@ int compute_nb(int n, int w) {
 
 // CTAs per pivot block of the Gram kernels (a cluster splitting the rows): the FP64 Gram is
 // bound by the FP64 mma rate and takes every SM it can (>= 16 rows per CTA); the FP32 Gram is
-// ~64x cheaper per row, so its CTAs keep >= 128 rows and the cluster reduction stays short.
+// ~64x cheaper per row, so its CTAs keep >= 64 rows and the cluster reduction stays short
+// (measured on the 512 x 512 workload: 64 rows per CTA beat 32, 128, 256 and 512).
 int choose_cluster(int half, int mp, int min_rows) {
   int cs = 1;
   while (cs * 2 <= 16 && half * cs * 2 <= 2 * 152 && mp / (cs * 2) >= min_rows) cs *= 2;
@@ -517,7 +518,7 @@ int solve_real(int m, int n, int dtype, void* Gv, int ldg, const int8_t* Jdev, c
     ++launches;
     ck(cudaGetLastError());
   }
-  const int CS = choose_cluster(P.half, P.mp, 16), CS32 = choose_cluster(P.half, P.mp, 128);
+  const int CS = choose_cluster(P.half, P.mp, 16), CS32 = choose_cluster(P.half, P.mp, 64);
   const int gslabs = (P.mp + 63) / 64;
   const int tslabs = gslabs + (have_vw ? (P.np + 63) / 64 : 0);
   const int ew_blocks = std::min(1024, (int)(((size_t)P.mp * n + 255) / 256));
