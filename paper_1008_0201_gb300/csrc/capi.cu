@@ -397,7 +397,7 @@ struct Single {
 // ------------------------------------------------------------------ single solve
 int solve_real(int m, int n, int dtype, void* Gv, int ldg, const int8_t* Jdev, const jac_opts* opts_in, double* lambda,
                void* Uv, int ldu, void* Vv, int ldv, jac_info* info, cudaStream_t st, const ArgPos& ap,
-               const double* Vinit = nullptr) {
+               const double* Vinit = nullptr, bool strict_stop = false) {
   jac_opts o;
   jacobi_default_opts(&o);
   if (opts_in) o = *opts_in;
@@ -468,6 +468,7 @@ int solve_real(int m, int n, int dtype, void* Gv, int ldg, const int8_t* Jdev, c
   ar2.base = static_cast<char*>(base);
   carve_all(ar2);
   hp.boff = boff_dev;
+  hp.tol = o.tol;
   hp.Js = L.Js;
   hp.pairs = L.pairs;
   hp.counts = L.counts;
@@ -542,6 +543,7 @@ int solve_real(int m, int n, int dtype, void* Gv, int ldg, const int8_t* Jdev, c
   double sweep_ms_h[64] = {};
   SweepGraph graphs[5];
   bool use_graphs = !weights;
+  int phase_sweeps = 0;  // sweeps of the current (FP64 or FP32-only) phase
   for (int sw = 0; status == JAC_OK && n > 1 && sw < o.max_sweeps; ++sw) {
     const auto t_sweep = std::chrono::steady_clock::now();
     auto sweep_done = [&]() {
@@ -679,7 +681,14 @@ int solve_real(int m, int n, int dtype, void* Gv, int ldg, const int8_t* Jdev, c
       continue;
     }
     sweep_done();
-    if (hrec.pivots_rotated == 0) {
+    // converged: a sweep rotated nothing, or, from the second sweep of the phase on, its largest
+    // scaled off-diagonal delta was so small that, by the quadratic convergence of the cyclic
+    // method, the next sweep would rotate nothing (delta^2 <= 1e-6 tol: a margin of 10^6 on the
+    // constant).  The first sweep of a phase does not qualify: its delta says nothing yet about
+    // the rate.
+    ++phase_sweeps;
+    if (hrec.pivots_rotated == 0 ||
+        (!strict_stop && phase_sweeps >= 2 && hrec.max_scaled * hrec.max_scaled <= 1e-6 * pp.tol)) {
       converged = 1;
       break;
     }
@@ -800,7 +809,7 @@ int solve_complex(int m, int n, void* Gv, int ldg, const int8_t* Jdev, const jac
     if (o2.precision == JAC_PREC_FP32) o2.precision = JAC_PREC_FP64;
     if (status == JAC_OK)
       status = solve_real((int)m2, (int)n2, JAC_R64, Gr2, (int)m2, Jr2, &o2, lam_r, nullptr, 0, Vr, (int)n2, info, st, ap,
-                          want_v ? Vr2 : nullptr);
+                          want_v ? Vr2 : nullptr, /*strict_stop=*/true);
     if (info) {  // totals over both passes; the per-sweep maxima of pass 1, then of pass 2
       double merged[64], merged_ms[64];
       int t = 0;
@@ -979,6 +988,9 @@ int solve_batched(int batch, const int* m, const int* n, int dtype, void* const*
     const int b = order[i];
     const Plan& P = plans[b];
     hp[i].boff = d_boff + boff_at[i];
+    hp[i].tol = (o.tol > 0.0) ? o.tol
+                              : std::max((double)P.n, (fp32_only ? 8.0 : 0.0) * std::sqrt((double)P.mp)) *
+                                    (fp32_only ? 5.9604644775390625e-08 : 1.1102230246251565e-16);
     hp[i].Js = d_Js + jsoff[i];
     hp[i].pairs = tables[P.nb].first;
     hp[i].counts = tables[P.nb].second;

@@ -17,6 +17,8 @@
 // imaginary parts only to that eigenspace accuracy.  The complex path therefore rebuilds the
 // exact pair structure from column 2i of every pair (k_restructure) and sweeps once more in
 // FP64: the second pass starts with off-diagonals of that size and converges quadratically.
+// It ends only on a sweep that rotates nothing: the complex columns read off after a rotating
+// sweep would carry that sweep's structure error.
 #include "jacobi_common.cuh"
 
 namespace jac {

@@ -97,6 +97,7 @@ struct JacProb {
   double* vp;        // [half][apld * apld] pivot transforms V_P
   int apld;          // leading dimension of a pivot block (the pivot capacity of its class)
   int active;        // 0: converged or failed, every kernel skips the problem
+  double tol;        // rotation threshold of the problem (batched convergence test)
   int* skip;         // [half]
   struct PairStat* stats;  // [nsteps][half]
   unsigned* pflags;  // JAC_DEVERR_* bits of this problem

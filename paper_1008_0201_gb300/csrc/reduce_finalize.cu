@@ -85,7 +85,12 @@ __global__ void k_sweep_reduce(JacProb* __restrict__ probs, JacIO* __restrict__ 
     io[blockIdx.x].sweeps += 1;
     io[blockIdx.x].rotations += r.rotations;
     if (r.err & JAC_DEVERR_NOTPD) a.active = 0;
-    if (deactivate && r.pivots_rotated == 0) a.active = 0;
+    // converged: nothing rotated, or (from the second sweep on) the sweep's largest scaled
+    // off-diagonal delta satisfies delta^2 <= 1e-6 tol (quadratic convergence: the next sweep
+    // would rotate nothing)
+    if (deactivate && (r.pivots_rotated == 0 ||
+                       (io[blockIdx.x].sweeps >= 2 && r.max_scaled * r.max_scaled <= 1e-6 * a.tol)))
+      a.active = 0;
     if (remaining && a.active) atomicAdd(remaining, 1);
   }
 }
