@@ -47,9 +47,19 @@ __global__ void __launch_bounds__(128) k_gram32(const JacProb* __restrict__ prob
   for (int r0 = r_begin; r0 < r_end; r0 += G32_RS) {
     const int rs = min(G32_RS, r_end - r0);
     __syncthreads();
-    for (int idx = tid; idx < JAC_KMAX * G32_RS; idx += 128) {
-      const int c = idx / G32_RS, r = idx % G32_RS;
-      Xs[r][c] = (c < k && r < rs) ? G32[(size_t)pcol(c, wp, op, oq) * a.mp + r0 + r] : 0.0f;
+    {  // loads first, then stores: one global latency per slab
+      constexpr int NLD = JAC_KMAX * G32_RS / 128;
+      float v[NLD];
+#pragma unroll
+      for (int u = 0; u < NLD; ++u) {
+        const int idx = tid + u * 128, c = idx / G32_RS, r = idx % G32_RS;
+        v[u] = (c < k && r < rs) ? __ldg(G32 + (size_t)pcol(c, wp, op, oq) * a.mp + r0 + r) : 0.0f;
+      }
+#pragma unroll
+      for (int u = 0; u < NLD; ++u) {
+        const int idx = tid + u * 128;
+        Xs[idx % G32_RS][idx / G32_RS] = v[u];
+      }
     }
     __syncthreads();
     for (int r = 0; r < rs; ++r) {
@@ -117,13 +127,29 @@ __global__ void __launch_bounds__(256) k_update32(const JacProb* __restrict__ pr
   if (rs <= 0) return;
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
   const double* V = a.vp + (size_t)pair * a.apld * a.apld;
-  for (int idx = tid; idx < JAC_KMAX * JAC_KMAX; idx += 256) {
-    const int c = idx % JAC_KMAX, j = idx / JAC_KMAX;
-    Bs[c][j] = (c < k && j < k) ? (float)V[j * a.apld + c] : 0.0f;
-  }
-  for (int idx = tid; idx < JAC_KMAX * 64; idx += 256) {
-    const int r = idx % 64, c = idx / 64;
-    Xs[r][c] = (c < k && r < rs) ? base[(size_t)pcol(c, wp, op, oq) * ld + r0 + r] : 0.0f;
+  {  // all loads of the thread first, then the stores: one global latency, not one per element
+    constexpr int NB = JAC_KMAX * JAC_KMAX / 256, NX = JAC_KMAX * 64 / 256;
+    float vb[NB], vx[NX];
+#pragma unroll
+    for (int u = 0; u < NB; ++u) {
+      const int idx = tid + u * 256, c = idx % JAC_KMAX, j = idx / JAC_KMAX;
+      vb[u] = (c < k && j < k) ? (float)__ldg(V + j * a.apld + c) : 0.0f;
+    }
+#pragma unroll
+    for (int u = 0; u < NX; ++u) {
+      const int idx = tid + u * 256, r = idx % 64, c = idx / 64;
+      vx[u] = (c < k && r < rs) ? base[(size_t)pcol(c, wp, op, oq) * ld + r0 + r] : 0.0f;
+    }
+#pragma unroll
+    for (int u = 0; u < NB; ++u) {
+      const int idx = tid + u * 256;
+      Bs[idx % JAC_KMAX][idx / JAC_KMAX] = vb[u];
+    }
+#pragma unroll
+    for (int u = 0; u < NX; ++u) {
+      const int idx = tid + u * 256;
+      Xs[idx % 64][idx / 64] = vx[u];
+    }
   }
   __syncthreads();
   float acc[4][4];

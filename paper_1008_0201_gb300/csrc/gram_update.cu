@@ -53,12 +53,24 @@ __global__ void __launch_bounds__(128) k_gram(const JacProb* __restrict__ probs,
   for (int r0 = r_begin; r0 < r_end; r0 += GRAM_RS) {
     const int rs = min(GRAM_RS, r_end - r0);  // multiple of 16
     __syncthreads();
-    // load the slab: column c rows r0..r0+rs-1 (zero columns k..KP-1)
-    for (int idx = threadIdx.x; idx < KP * (rs / 2); idx += blockDim.x) {
-      const int c = idx / (rs / 2), rr = (idx % (rs / 2)) * 2;
-      double2 v = make_double2(0.0, 0.0);
-      if (c < k) v = __ldg(reinterpret_cast<const double2*>(a.Gw + (size_t)pair_col(c, wp, op, oq) * a.mp + r0 + rr));
-      *reinterpret_cast<double2*>(Xs + c * GRAM_LDS + rr) = v;
+    // load the slab: column c rows r0..r0+rs-1 (zero columns k..KP-1); all of a thread's loads
+    // are issued before its stores
+    {
+      constexpr int NLD = JAC_KMAX * (GRAM_RS / 2) / 128;
+      const int tot = KP * (rs / 2);
+      double2 v[NLD];
+#pragma unroll
+      for (int u = 0; u < NLD; ++u) {
+        const int idx = threadIdx.x + u * 128, c = idx / (rs / 2), rr = (idx % (rs / 2)) * 2;
+        v[u] = (idx < tot && c < k)
+                   ? __ldg(reinterpret_cast<const double2*>(a.Gw + (size_t)pair_col(c, wp, op, oq) * a.mp + r0 + rr))
+                   : make_double2(0.0, 0.0);
+      }
+#pragma unroll
+      for (int u = 0; u < NLD; ++u) {
+        const int idx = threadIdx.x + u * 128, c = idx / (rs / 2), rr = (idx % (rs / 2)) * 2;
+        if (idx < tot) *reinterpret_cast<double2*>(Xs + c * GRAM_LDS + rr) = v[u];
+      }
     }
     __syncthreads();
     for (int kk = 0; kk < rs; kk += 16) {

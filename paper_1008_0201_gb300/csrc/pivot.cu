@@ -126,9 +126,21 @@ __global__ void __launch_bounds__((KM / 2) * LPP, 1)
 
   // ---- 1. load A_P, scaled matrix E, statistics ----------------------------------------------
   const double* A = a.Ap + (size_t)pair * a.apld * a.apld;
-  for (int e = tid; e < k * k; e += NT) {
-    const int i = e % k, j = e / k;
-    Vs[j * LDV + i] = A[j * a.apld + i];
+  {
+    // all of a thread's loads are issued before its stores: the global (L2) latency is paid
+    // once, not once per element
+    constexpr int NLD = (KM * KM + NT - 1) / NT;
+    double v[NLD];
+#pragma unroll
+    for (int u = 0; u < NLD; ++u) {
+      const int e = tid + u * NT;
+      v[u] = (e < k * k) ? __ldg(A + (e / k) * a.apld + e % k) : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < NLD; ++u) {
+      const int e = tid + u * NT;
+      if (e < k * k) Vs[(e / k) * LDV + e % k] = v[u];
+    }
   }
   if (tid == 0) sm.bad = 0;
   __syncthreads();
