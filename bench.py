@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--factor", default="chol_signpiv")
     ap.add_argument("--block-mode", default="oriented", choices=["full", "oriented"])
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp32_only"])
+    ap.add_argument("--f64-products", default="mma", choices=["mma", "split16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-other-workloads", action="store_true")
     ap.add_argument("--workload", default="c2", choices=["c2", "paper_e1"],
@@ -311,7 +312,8 @@ def paper_e1(args):
     Gd = torch.from_numpy(G).to(dev)
     Jd = torch.from_numpy(J).to(dev)
     opts = binding.default_opts(block_w=BLOCK_W, ordering=args.ordering, factor=args.factor,
-                                block_mode=args.block_mode, precision=args.precision)
+                                block_mode=args.block_mode, precision=args.precision,
+                                f64_products=args.f64_products)
     stream = torch.cuda.current_stream(dev)
     binding.jacobi_hsvd(Gd, Jd, opts, want_u=False)  # warm-up (builds the graphs of this size once)
     torch.cuda.synchronize()
@@ -369,7 +371,8 @@ def main():
     G, J = replica_input(rank)
     m, n = G.shape
     opts = binding.default_opts(block_w=BLOCK_W, ordering=args.ordering, factor=args.factor,
-                                block_mode=args.block_mode, precision=args.precision)
+                                block_mode=args.block_mode, precision=args.precision,
+                                f64_products=args.f64_products)
     stream = torch.cuda.current_stream(dev)
     sptr = stream.cuda_stream
     # inputs resident in HBM: one fresh column-major copy per step (G is overwritten in place)
@@ -499,6 +502,7 @@ def main():
             "config": {"workload": WORKLOAD + ", " + variant_name(args), "n": n, "block_w": BLOCK_W,
                        "ordering": args.ordering,
                        "factor": args.factor, "block_mode": args.block_mode, "precision": args.precision,
+                       "f64_products": args.f64_products,
                        "sweeps": info["sweeps"],
                        "sweep_ms": ["%.2f" % x for x in info["sweep_ms"]],
                        "fp32_sweeps": info["lowp_sweeps"], "steps_per_sweep": info["steps_per_sweep"],

@@ -93,6 +93,14 @@ enum jac_precision {
                             smallest scaled off-diagonal an FP32 Gram of m rows resolves */
 };
 
+/* Arithmetic of the FP64 Gram, update and V_P J-orthogonality products (FP64 sweeps). */
+enum jac_f64_products {
+  JAC_F64_MMA = 0,    /* FP64 tensor-core mma (m16n8k16 f64) */
+  JAC_F64_SPLIT16 = 1 /* exact FP16 tensor-core products of 7-bit digit slices of each operand,
+                         8 slices, recombined in FP64 (error-free splitting after Ozaki et al.):
+                         each product term exact to 2^-53 of its operand group bounds */
+};
+
 typedef struct {
   int block_w;     /* target block-column width w; nb = max(2, 2*ceil(n/(2w))) blocks whose
                       widths differ by at most one (Sec. 3).  1 <= w <= 32 in this version. */
@@ -103,6 +111,7 @@ typedef struct {
   int max_sweeps;  /* >= 1 */
   int want_v;      /* 1: accumulate and return V (n x n); 0: V is not touched */
   double tol;      /* rotate a pair (i,j) iff |a_ij| > tol sqrt(a_ii a_jj); <= 0 selects n*2^-53 */
+  int f64_products;/* enum jac_f64_products */
 } jac_opts;
 
 typedef struct {
@@ -127,7 +136,7 @@ typedef struct {
 } jac_info;
 
 /* Fills *opts with the defaults: w = 32, round-robin, full block, sign-pivoted Cholesky,
- * FP64, max_sweeps = 50, want_v = 1, tol = n*2^-53 (tol <= 0). */
+ * FP64, max_sweeps = 50, want_v = 1, tol = n*2^-53 (tol <= 0), FP64 products JAC_F64_MMA. */
 void jacobi_default_opts(jac_opts* opts);
 
 /* Short text for a return code. */

@@ -19,12 +19,13 @@ ORDER = {"modulus": 0, "modulus_mod": 1, "round_robin": 2, "cycle_weight": 3}
 FACTOR = {"chol": 0, "chol_diagpiv": 1, "chol_signpiv": 2}
 PRECISION = {"fp64": 0, "fp32": 1, "fp32_only": 2}
 BLOCK_MODE = {"full": 0, "oriented": 1}
+F64_PRODUCTS = {"mma": 0, "split16": 1}
 
 
 class JacOpts(ctypes.Structure):
     _fields_ = [("block_w", ctypes.c_int), ("ordering", ctypes.c_int), ("block_mode", ctypes.c_int),
                 ("factor", ctypes.c_int), ("precision", ctypes.c_int), ("max_sweeps", ctypes.c_int),
-                ("want_v", ctypes.c_int), ("tol", ctypes.c_double)]
+                ("want_v", ctypes.c_int), ("tol", ctypes.c_double), ("f64_products", ctypes.c_int)]
 
 
 class JacInfo(ctypes.Structure):
@@ -114,6 +115,8 @@ def default_opts(**kw):
             val = PRECISION[val]
         elif key == "block_mode" and isinstance(val, str):
             val = BLOCK_MODE[val]
+        elif key == "f64_products" and isinstance(val, str):
+            val = F64_PRODUCTS[val]
         setattr(o, key, val)
     return o
 

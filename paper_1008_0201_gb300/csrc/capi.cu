@@ -55,6 +55,10 @@ __global__ void k_complexify(int m, int n, const double* Gr, const double* lam_r
                              double* lambda, double2* U, int ldu, double2* V, int ldv, unsigned* bad);
 __global__ void k_restructure(int h, int n, const double* in, double* out, const double* lam, int8_t* Jout);
 __global__ void k_fill_uniform(double* x, long long n, unsigned long long seed);
+__global__ void k_gram_oz(const JacProb* probs, int s, int CS);
+__global__ void k_update_oz(const JacProb* probs, int s, int gslabs);
+size_t oz_gram_smem_bytes();
+size_t oz_update_smem_bytes();
 }  // namespace jac
 
 using namespace jac;
@@ -144,6 +148,11 @@ int setup_attributes(int dev) {
   ok &= cudaFuncSetAttribute(k_gram, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess;
   ok &= cudaFuncSetAttribute(k_gram32, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess;
   ok &= cudaFuncSetAttribute(k_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kUpdSmem) == cudaSuccess;
+  ok &= cudaFuncSetAttribute(k_gram_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_gram_smem_bytes()) ==
+        cudaSuccess;
+  ok &= cudaFuncSetAttribute(k_gram_oz, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess;
+  ok &= cudaFuncSetAttribute(k_update_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_update_smem_bytes()) ==
+        cudaSuccess;
   ok &= pivot_set_attributes() == 0;
   ok &= pivot64_set_attributes() == 0;
   ok &= cudaFuncSetAttribute(k_rank, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024) == cudaSuccess;
@@ -180,6 +189,7 @@ int check_opts(const jac_opts& o, int argpos, bool batch) {
   if (batch && o.precision == JAC_PREC_FP32) return -argpos;
   if (o.max_sweeps < 1) return -argpos;
   if (o.want_v != 0 && o.want_v != 1) return -argpos;
+  if (o.f64_products != JAC_F64_MMA && o.f64_products != JAC_F64_SPLIT16) return -argpos;
   return 0;
 }
 
@@ -307,6 +317,9 @@ int launch_step(JacProb* dprobs, int count, int km, int max_half, int gslabs, in
   size_t pm = prof.pre(JAC_KERNEL_GRAM, st);
   if (lowp)
     r = launch_cluster(k_gram32, dim3(max_half * CS32, count), CS32, 128, 0, st, (const JacProb*)dprobs, s, CS32);
+  else if (pp.oz)
+    r = launch_cluster(k_gram_oz, dim3(max_half * CS, count), CS, 256, oz_gram_smem_bytes(), st,
+                       (const JacProb*)dprobs, s, CS);
   else
     r = launch_cluster(k_gram, dim3(max_half * CS, count), CS, 128, kGramSmem, st, (const JacProb*)dprobs, s, CS);
   prof.post(pm, st);
@@ -318,6 +331,8 @@ int launch_step(JacProb* dprobs, int count, int km, int max_half, int gslabs, in
   pm = prof.pre(JAC_KERNEL_UPDATE, st);
   if (lowp)
     k_update32<<<dim3(max_half, tslabs, count), 256, 0, st>>>(dprobs, s, gslabs);
+  else if (pp.oz)
+    k_update_oz<<<dim3(max_half, tslabs, count), 256, oz_update_smem_bytes(), st>>>(dprobs, s, gslabs);
   else
     k_update<<<dim3(max_half, tslabs, count), 128, kUpdSmem, st>>>(dprobs, s, gslabs);
   prof.post(pm, st);
@@ -519,7 +534,9 @@ int solve_real(int m, int n, int dtype, void* Gv, int ldg, const int8_t* Jdev, c
     ++launches;
     ck(cudaGetLastError());
   }
-  const int CS = choose_cluster(P.half, P.mp, 16), CS32 = choose_cluster(P.half, P.mp, 64);
+  // the digit-product Gram is ~20x cheaper per row than the FP64 mma one: >= 32 rows per CTA
+  const int CS = choose_cluster(P.half, P.mp, o.f64_products == JAC_F64_SPLIT16 ? 32 : 16),
+            CS32 = choose_cluster(P.half, P.mp, 64);
   const int gslabs = (P.mp + 63) / 64;
   const int tslabs = gslabs + (have_vw ? (P.np + 63) / 64 : 0);
   const int ew_blocks = std::min(1024, (int)(((size_t)P.mp * n + 255) / 256));
@@ -559,6 +576,7 @@ int solve_real(int m, int n, int dtype, void* Gv, int ldg, const int8_t* Jdev, c
     pp.factor = o.factor;
     pp.ns_mode = low ? 0 : 1;
     pp.oriented = (o.block_mode == JAC_BLOCK_ORIENTED) ? 1 : 0;
+    pp.oz = (o.f64_products == JAC_F64_SPLIT16) ? 1 : 0;
     if (weights) {
       const int npairs = P.nb * (P.nb - 1) / 2;
       if (!low) {
@@ -1060,6 +1078,7 @@ int solve_batched(int batch, const int* m, const int* n, int dtype, void* const*
   pp.factor = o.factor;
   pp.ns_mode = fp32_only ? 0 : 1;
   pp.oriented = (o.block_mode == JAC_BLOCK_ORIENTED) ? 1 : 0;
+  pp.oz = (o.f64_products == JAC_F64_SPLIT16) ? 1 : 0;
   ProfRun prof;
   prof.begin();
   long long launches = 0;
@@ -1158,6 +1177,7 @@ void jacobi_default_opts(jac_opts* o) {
   o->max_sweeps = 50;
   o->want_v = 1;
   o->tol = 0.0;
+  o->f64_products = JAC_F64_MMA;
 }
 
 const char* jacobi_status_string(int s) {

@@ -132,6 +132,7 @@ struct PivotParams {
   int factor;        // 0 unpivoted, 2 sign-pivoted
   int ns_mode;       // 1: make V_P J-unitary in FP64 (Newton-Schulz); 0: leave the FP32 transform
   int oriented;      // 1: block-oriented inner sweep (one sweep; cross block only after step 0)
+  int oz;            // FP64 Gram / update / V_P residual from exact FP16 digit products (ozaki.cuh)
 };
 
 // per (step, pair) record written by the pivot kernel, reduced per sweep
