@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(256) k_gram_oz(const JacProb* __restrict__ pro
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
         const int i = 16 * ti + g + 8 * (v >> 1), j = 8 * tj + 2 * t4 + (v & 1);
-        tot[u][v] += ldexp(oz_combine(acc, v), sm.E[i] + sm.E[j] - 2056);
+        tot[u][v] += oz_value(acc, v, sm.E[i] + sm.E[j] - 2056);
       }
     }
   }
@@ -347,8 +347,8 @@ __global__ void __launch_bounds__(256) k_update_oz(const JacProb* __restrict__ p
       for (int e = 0; e < 4; ++e) {
         const int r = 16 * ti + g + 8 * (e >> 1), c = 8 * (tj0 + hh) + 2 * t4 + (e & 1);
         if (r < rs && c < k) {
-          const double sum = hh ? oz_combine(acc1, e) : oz_combine(acc0, e);
-          base[(size_t)oz_pair_col(c, wp, op, oq) * ld + r0 + r] = ldexp(sum, sm.rexp[r] + sm.vexp[c] - 2056);
+          const int E = sm.rexp[r] + sm.vexp[c] - 2056;
+          base[(size_t)oz_pair_col(c, wp, op, oq) * ld + r0 + r] = hh ? oz_value(acc1, e, E) : oz_value(acc0, e, E);
         }
       }
     }

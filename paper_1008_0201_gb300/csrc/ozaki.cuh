@@ -104,13 +104,35 @@ __device__ __forceinline__ void oz_levels(float (&acc)[NL][4], const unsigned (&
       oz_mma(acc[L], fa[t], fb[L - t][0], fb[L - t][1]);
 }
 
-// sum_L acc_L 2^(-7 L) in FP64 (each term exact), smallest level first
+// GB300 issues ~1.6 FP64 operations per clock per SM (FP32: 128), so the recombination avoids
+// FP64 work: the integer level sums are gathered exactly in two int64 (hi: L = 0..3 in units of
+// level 3, lo: L = 4..NL-1 in units of level NL-1, both below 2^51 for level sums below 2^23),
+// turned into doubles by the exponent-bias trick and joined with one rounding: 4 FP64
+// operations per value, against ~25 for a per-level sum and ldexp.
+
+// exact double of an integer |x| < 2^51: the bits of 1.5 * 2^52 + x are those of 1.5 * 2^52
+// plus x
+__device__ __forceinline__ double oz_i2d(long long x) {
+  return __longlong_as_double(0x4338000000000000ll + x) - 6755399441055744.0;
+}
+
+// 2^E sum_L acc_L 2^(-7 L), the acc_L exact integers held in FP32
 template <int NL>
-__device__ __forceinline__ double oz_combine(const float (&acc)[NL][4], int v) {
-  double s = 0.0;
+__device__ __forceinline__ double oz_value(const float (&acc)[NL][4], int v, int E) {
+  static_assert(NL > 4 && NL <= 9, "two int64 accumulators");
+  long long hi = 0, lo = 0;
 #pragma unroll
-  for (int L = NL - 1; L >= 0; --L) s += (double)acc[L][v] * (1.0 / (double)(1ull << (7 * L)));
-  return s;
+  for (int L = 0; L < 4; ++L) hi = hi * 128 + __float2int_rn(acc[L][v]);
+#pragma unroll
+  for (int L = 4; L < NL; ++L) lo = lo * 128 + __float2int_rn(acc[L][v]);
+  const double s = fma(oz_i2d(hi), (double)(1ll << (7 * (NL - 4))), oz_i2d(lo));
+  const int e = E - 7 * (NL - 1);
+  return (e >= -1022 && e <= 1023) ? s * __longlong_as_double((long long)(e + 1023) << 52) : ldexp(s, e);
+}
+
+// x or -x by the sign bit (no FP64 operation)
+__device__ __forceinline__ double oz_neg_if(double x, bool neg) {
+  return __longlong_as_double(__double_as_longlong(x) ^ ((long long)neg << 63));
 }
 
 }  // namespace jac

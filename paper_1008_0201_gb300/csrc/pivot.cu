@@ -26,6 +26,7 @@
 // otherwise on the FP64 mma path (symmetric tiles only); the correction product itself is small
 // and is formed in FP32.
 #include "jacobi_common.cuh"
+#include "ozaki.cuh"
 
 namespace jac {
 
@@ -39,8 +40,14 @@ struct PivotSmem {
   static constexpr int NW = NT / 32;
   static constexpr int P2 = KM / 2;    // pair slots
   static constexpr int MBS = 2 * KM + 8;  // mailbox slot: F and W column; +8 floats spreads banks
+  static constexpr int LDD = KM + 8;   // digit rows of W (halves): 16-byte aligned, ldmatrix conflict-free
   double V[KM * LDV];   // A_P first, then V (physical coordinates), FP64
-  double M[KM * LDV];   // FP64 residual
+  union {
+    double M[KM * LDV];           // FP64 residual (FP64 mma products)
+    __half D[OZ_T][KM][LDD];      // digits of W = V - I by column (digit products)
+  };
+  double dlo[KM];       // V_ii - 1 - fl(V_ii - 1) (digit products)
+  int dexp[KM];         // bound exponent of column c of W (digit products)
   float S[KM * LDS];    // Cholesky working matrix (upper triangle), later FP32 J M
   float F[KM * LDF];
   float W[KM * LDF];
@@ -94,6 +101,123 @@ __device__ __forceinline__ float col_entry(const float (&f)[R], int r, int group
 #pragma unroll
   for (int u = 1; u < R; ++u) v = ((r & (R - 1)) == u) ? f[u] : v;
   return __shfl_sync(0xffffffffu, v, group_lane0 + r / R);
+}
+
+// J-orthogonality residual M = V^T J V - J from digit products (ozaki.cuh).  With W = fl(V - I)
+// column by column and l_i = (V_ii - 1) - W_ii exactly (TwoSum), V = I + W + diag(l) and
+//   M = W^T J + J W + W^T J W + diag(2 J l) + diag(l) J W + W^T J diag(l)   (+ l^2 terms, dropped)
+// The linear and diag(l) terms are elementwise FP64; W^T J W, of size |W|^2, runs on the digit
+// path with the columns of W (over the k rows) as scale groups and J_r applied to the A digits
+// by their sign bit.  So M is accurate to ~2^-53 |W|^2 + 2^-53 |W|, where the FP64 product
+// V^T J V carries ~2^-53 |V|^2.  Writes S = fp32(J M) (zero outside k x k) and returns this
+// thread's max |M_ij|.  Warp w prepares columns 8w..8w+7 (lane: rows lane, lane + 32).
+template <int KM, int LPP>
+__device__ float oz_residual(PivotSmem<KM, LPP>& sm, const double* Vs, int k, int KP) {
+  using SM = PivotSmem<KM, LPP>;
+  constexpr int NW = SM::NW, LDV = SM::LDV, LDS = SM::LDS;
+  constexpr int RI = KM / 32;
+  static_assert(NW * 8 == KM, "one warp per 8 columns");
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t4 = lane & 3;
+  // ---- W, its column bounds and digits
+  double w[8][RI];
+#pragma unroll
+  for (int cc = 0; cc < 8; ++cc) {
+    const int c = 8 * warp + cc;
+#pragma unroll
+    for (int i = 0; i < RI; ++i) {
+      const int r = lane + 32 * i;
+      double x = (r < k && c < k) ? Vs[c * LDV + r] : 0.0;
+      if (r == c && r < k) {  // TwoSum(V_cc, -1)
+        const double hi = x - 1.0, bv = hi - x, av = hi - bv;
+        sm.dlo[c] = (x - av) + (-1.0 - bv);
+        x = hi;
+      }
+      w[cc][i] = x;
+    }
+  }
+  int ec[8];
+#pragma unroll
+  for (int cc = 0; cc < 8; ++cc) {
+    int e = 0;
+#pragma unroll
+    for (int i = 0; i < RI; ++i) e = max(e, oz_bexp(w[cc][i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+    ec[cc] = e;
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int cc = 0; cc < 8; ++cc) sm.dexp[8 * warp + cc] = ec[cc];
+  }
+#pragma unroll
+  for (int cc = 0; cc < 8; ++cc) {
+#pragma unroll
+    for (int i = 0; i < RI; ++i) {
+      __half d[OZ_T];
+      oz_split(oz_fixed(w[cc][i], oz_bexp(w[cc][i]) - ec[cc]), d);
+#pragma unroll
+      for (int t = 0; t < OZ_T; ++t) sm.D[t][8 * warp + cc][lane + 32 * i] = d[t];
+    }
+  }
+  __syncthreads();
+  // ---- upper 16 x 8 tiles of W^T J W, then M and S
+  float mloc = 0.0f;
+  const int ntj = KP / 8, ntiles = (KP / 16) * ntj;
+  for (int tile = warp; tile < ntiles; tile += NW) {
+    const int ti = tile / ntj, tj = tile % ntj;
+    if (8 * tj + 7 < 16 * ti) continue;
+    float acc[OZ_T][4];
+#pragma unroll
+    for (int L = 0; L < OZ_T; ++L)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[L][v] = 0.0f;
+    const int arow = 16 * ti + (lane & 7) + 8 * ((lane >> 3) & 1), akof = 8 * (lane >> 4);
+    const int brow = 8 * tj + (lane & 7), bkof = 8 * ((lane >> 3) & 1);
+    for (int kk = 0; kk < KP; kk += 16) {
+      const int r0 = kk + 2 * t4;
+      const unsigned slo = (sm.jphys[r0] < 0 ? 0x8000u : 0u) | (sm.jphys[r0 + 1] < 0 ? 0x80000000u : 0u);
+      const unsigned shi = (sm.jphys[r0 + 8] < 0 ? 0x8000u : 0u) | (sm.jphys[r0 + 9] < 0 ? 0x80000000u : 0u);
+      unsigned fa[OZ_T][4], fb[OZ_T][2];
+#pragma unroll
+      for (int t = 0; t < OZ_T; ++t) {
+        oz_ldsm4(fa[t], &sm.D[t][arow][kk + akof]);
+        fa[t][0] ^= slo;
+        fa[t][1] ^= slo;
+        fa[t][2] ^= shi;
+        fa[t][3] ^= shi;
+        oz_ldsm2(fb[t][0], fb[t][1], &sm.D[t][brow][kk + bkof]);
+      }
+      oz_levels(acc, fa, fb);
+    }
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int x = 16 * ti + g + 8 * (v >> 1), j = 8 * tj + 2 * t4 + (v & 1);
+      if (j < x) continue;  // (x, j), j >= x, covers the block; (j, x) is its mirror
+      float sxj = 0.0f, sjx = 0.0f;
+      if (x < k && j < k) {  // FP64 work kept to ~7 operations per entry (J by sign bits)
+        const bool nx = sm.jphys[x] < 0, nj = sm.jphys[j] < 0;
+        double m = oz_value(acc, v, sm.dexp[x] + sm.dexp[j] - 2056);
+        if (x == j) {
+          const double wxx = Vs[x * LDV + x] - 1.0, l = sm.dlo[x];
+          m += oz_neg_if(wxx + wxx, nx);
+          if (__double_as_longlong(l) << 1) m += oz_neg_if(2.0 * l * (1.0 + wxx), nx);
+        } else {
+          const double wxj = Vs[j * LDV + x], wjx = Vs[x * LDV + j];  // W[x][j], W[j][x]
+          const double lx = sm.dlo[x], lj = sm.dlo[j];
+          m += oz_neg_if(wjx, nj) + oz_neg_if(wxj, nx);
+          if ((__double_as_longlong(lx) << 1) | (__double_as_longlong(lj) << 1))
+            m += oz_neg_if(lx * wxj, nx) + oz_neg_if(lj * wjx, nj);
+        }
+        const float f = (float)m;
+        mloc = fmaxf(mloc, fabsf(f));
+        sxj = nx ? -f : f;  // (J M)[x][j]
+        sjx = nj ? -f : f;  // (J M)[j][x]
+      }
+      sm.S[j * LDS + x] = sxj;
+      sm.S[x * LDS + j] = sjx;
+    }
+  }
+  return mloc;
 }
 
 template <int KM, int LPP>
@@ -645,6 +769,8 @@ __global__ void __launch_bounds__((KM / 2) * LPP, 1)
           mloc = fmaxf(mloc, fabsf(mv));
           sm.S[j * LDS + x] = (x < k) ? (float)sm.jphys[x] * mv : 0.0f;  // (J M)[x][j]
         }
+      } else if (pp.oz) {
+        mloc = oz_residual<KM, LPP>(sm, Vs, k, KP);
       } else {
         // FP64 mma, upper tiles (8 tj + 7 >= 16 ti) and the mirror of the strict lower part
         const int g = lane >> 2, t = lane & 3;
@@ -754,6 +880,7 @@ __global__ void __launch_bounds__((KM / 2) * LPP, 1)
 // Lanes per pair slot of each pivot capacity: KM = 64 -> 8 lanes x 8 rows, 256 threads;
 // KM = 32 -> 8 lanes x 4 rows, 128 threads.
 constexpr int kLpp64 = 8, kLpp32 = 8;
+static_assert(sizeof(PivotSmem<64, kLpp64>) <= 232448, "pivot shared memory above the 227 KB per-CTA limit");
 
 size_t pivot_smem_bytes(int km) {
   return km == 32 ? sizeof(PivotSmem<32, kLpp32>) : sizeof(PivotSmem<64, kLpp64>);
