@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--factor", default="chol_signpiv")
     ap.add_argument("--block-mode", default="oriented", choices=["full", "oriented"])
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp32_only"])
-    ap.add_argument("--f64-products", default="mma", choices=["mma", "split16"])
+    ap.add_argument("--f64-products", default="split16", choices=["mma", "split16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-other-workloads", action="store_true")
     ap.add_argument("--workload", default="c2", choices=["c2", "paper_e1"],

@@ -136,7 +136,7 @@ typedef struct {
 } jac_info;
 
 /* Fills *opts with the defaults: w = 32, round-robin, full block, sign-pivoted Cholesky,
- * FP64, max_sweeps = 50, want_v = 1, tol = n*2^-53 (tol <= 0), FP64 products JAC_F64_MMA. */
+ * FP64, max_sweeps = 50, want_v = 1, tol = n*2^-53 (tol <= 0), FP64 products JAC_F64_SPLIT16. */
 void jacobi_default_opts(jac_opts* opts);
 
 /* Short text for a return code. */
@@ -155,7 +155,9 @@ int jacobi_version(void);
  *                  as the real one of twice the order, G_r = [X -Y; Y X] for G = X + iY and
  *                  J_r = diag(J, J), whose spectrum is that of H twice; the complex results are
  *                  read off every other column (JAC_EINTERNAL if the two copies of an eigenvalue
- *                  differ by more than 1e-6 relative).
+ *                  differ by more than 1e-6 relative).  opts->tol bounds the complex scaled
+ *                  off-diagonal entries: the real sweep rotates above tol / sqrt(2), as the real
+ *                  and imaginary parts of a complex entry are two real Gram entries.
  *  4 G, 5 ldg      device, in/out.  On return G = G_in V: the unnormalized U Sigma, columns in
  *                  output order.
  *  6 J             device int8[n], entries +1 / -1, any order (sorted internally to

@@ -774,11 +774,13 @@ int solve_complex(int m, int n, void* Gv, int ldg, const int8_t* Jdev, const jac
   if (Vv && ldv < n) return fail_arg(ap.ldv);
   const bool want_v = o.want_v != 0;
   // the rotation threshold is that of the complex problem of order n (tol <= 0: n eps), not of
-  // the real one of order 2n: both copies of a complex column pair are then orthogonal to the
-  // other columns to the complex problem's tolerance
+  // the real one of order 2n.  A complex entry g_i^* g_j has its real and imaginary parts in
+  // two real Gram entries (columns [x_i; y_i] against [x_j; y_j] and [-y_j; x_j]), so the real
+  // sweep uses tol / sqrt(2): every complex scaled off-diagonal entry then ends below tol
   if (o.tol <= 0.0)
     o.tol = (o.precision == JAC_PREC_FP32_ONLY) ? std::max((double)n, 8.0 * std::sqrt((double)m)) * 5.9604644775390625e-08
                                                 : (double)n * 1.1102230246251565e-16;
+  o.tol *= 0.70710678118654752;
   const size_t m2 = 2 * (size_t)m, n2 = 2 * (size_t)n;
   double *Gr = nullptr, *Gr2 = nullptr, *lam_r = nullptr, *Vr = nullptr, *Vr2 = nullptr;
   int8_t *Jr = nullptr, *Jr2 = nullptr;
@@ -1177,7 +1179,7 @@ void jacobi_default_opts(jac_opts* o) {
   o->max_sweeps = 50;
   o->want_v = 1;
   o->tol = 0.0;
-  o->f64_products = JAC_F64_MMA;
+  o->f64_products = JAC_F64_SPLIT16;
 }
 
 const char* jacobi_status_string(int s) {

@@ -130,6 +130,14 @@ __device__ __forceinline__ double oz_value(const float (&acc)[NL][4], int v, int
   return (e >= -1022 && e <= 1023) ? s * __longlong_as_double((long long)(e + 1023) << 52) : ldexp(s, e);
 }
 
+// (double)f by integer operations (FP32 subnormals flush to zero)
+__device__ __forceinline__ double oz_f2d(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xffu;
+  if (e == 0) return __hiloint2double((int)(u & 0x80000000u), 0);
+  return __hiloint2double((int)((u & 0x80000000u) | ((e + 896u) << 20) | ((u >> 3) & 0xfffffu)), (int)(u << 29));
+}
+
 // x or -x by the sign bit (no FP64 operation)
 __device__ __forceinline__ double oz_neg_if(double x, bool neg) {
   return __longlong_as_double(__double_as_longlong(x) ^ ((long long)neg << 63));

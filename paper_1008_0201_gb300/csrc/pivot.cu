@@ -739,9 +739,10 @@ __global__ void __launch_bounds__((KM / 2) * LPP, 1)
   for (int e = tid; e < KP * KP; e += NT) {
     const int r = e % KP, c = e / KP;
     const float w = (r < k && c < k) ? sm.W[c * LDF + r] : 0.0f;
-    const double v = (double)w + ((r == c && r < k) ? 1.0 : 0.0);
-    Vs[c * LDV + r] = v;
-    sm.Vf[c * LDS + r] = (float)v;
+    const bool diag = (r == c && r < k);
+    const double v = oz_f2d(w);  // integer conversion: FP64 instructions are scarce on GB300
+    Vs[c * LDV + r] = diag ? v + 1.0 : v;
+    sm.Vf[c * LDS + r] = diag ? w + 1.0f : w;
     wm = fmaxf(wm, fabsf(w));
   }
   int ns = 0;
@@ -814,12 +815,40 @@ __global__ void __launch_bounds__((KM / 2) * LPP, 1)
         ns_ok = true;
         break;
       }
-      // V <- V - V (J M) / 2: the correction is O(|M|), formed in FP32 from the FP32 copy of V
-      for (int e = tid; e < KP * KP; e += NT) {
-        const int r = e % KP, j = e / KP;
-        float sum = 0.0f;
-        for (int x = 0; x < k; ++x) sum = fmaf(sm.Vf[x * LDS + r], sm.S[j * LDS + x], sum);
-        Vs[j * LDV + r] -= 0.5 * (double)sum;
+      // V <- V - V (J M) / 2: the correction is O(|M|), formed in FP32 from the FP32 copy of V;
+      // each thread a 4 x CB block (rows rg + RG i, columns cg + CGN c) of the product, so a
+      // shared-memory load feeds 4 or CB FMAs; the FP32 copy follows V in FP32
+      {
+        constexpr int RG = KM / 4, CGN = NT / RG, CB = KM / CGN;
+        static_assert(RG * CGN == NT && CGN * CB == KM, "correction blocking");
+        const int rg = tid % RG, cg = tid / RG;
+        float sum[4][CB];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int c = 0; c < CB; ++c) sum[i][c] = 0.0f;
+        for (int x = 0; x < k; ++x) {
+          float vf[4], sv[CB];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) vf[i] = sm.Vf[x * LDS + rg + RG * i];
+#pragma unroll
+          for (int c = 0; c < CB; ++c) sv[c] = sm.S[(cg + CGN * c) * LDS + x];
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int c = 0; c < CB; ++c) sum[i][c] = fmaf(vf[i], sv[c], sum[i][c]);
+        }
+        __syncthreads();  // every read of Vf done
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int c = 0; c < CB; ++c) {
+            const int r = rg + RG * i, j = cg + CGN * c;
+            if (r < KP && j < KP) {
+              Vs[j * LDV + r] -= oz_f2d(0.5f * sum[i][c]);
+              sm.Vf[j * LDS + r] -= 0.5f * sum[i][c];
+            }
+          }
       }
       ++ns;
       __syncthreads();
@@ -828,11 +857,6 @@ __global__ void __launch_bounds__((KM / 2) * LPP, 1)
         ns_ok = true;
         break;
       }
-      for (int e = tid; e < KP * KP; e += NT) {
-        const int r = e % KP, c = e / KP;
-        sm.Vf[c * LDS + r] = (float)Vs[c * LDV + r];
-      }
-      __syncthreads();
     }
   } else {
     __syncthreads();

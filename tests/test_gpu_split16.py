@@ -1,4 +1,5 @@
-"""FP64 products from exact FP16 digit products (f64_products="split16") vs the CPU oracle.
+"""The two FP64 product paths vs the CPU oracle: exact FP16 digit products (f64_products =
+"split16", the default) and FP64 tensor-core mma ("mma").
 
 The Gram, update and V_P residual products of the FP64 sweeps run as sums of exact FP16 x FP16
 tensor-core products of 7-bit digit slices (error-free splitting after Ozaki et al.); each
@@ -93,7 +94,7 @@ def test_split16_agrees_with_mma(cuda_dev):
 
     G, J = inputs.config2_hyperbolic(n=256, salt=5)
     a = run(G, J, cuda_dev, block_w=32, **S16)
-    b = run(G, J, cuda_dev, block_w=32)
+    b = run(G, J, cuda_dev, block_w=32, f64_products="mma")
     assert a["status"] == 0 and b["status"] == 0
     B = G / np.linalg.norm(G, axis=0)
     kappa = np.linalg.cond(B) ** 2
@@ -118,7 +119,7 @@ def test_split16_batched(cuda_dev):
     check_all(Gs, Js, outs)
 
 
-def test_split16_complex(cuda_dev):
+def _complex_graded(dev, **kw):
     import torch
 
     from paper_1008_0201_gb300 import binding
@@ -129,10 +130,45 @@ def test_split16_complex(cuda_dev):
     G = G * (10.0 ** np.linspace(0, -3, n))[None, :]
     J = np.ones(n, dtype=np.int8)
     J[g.choice(n, size=15, replace=False)] = -1
-    opts = binding.default_opts(block_w=8, **S16)
-    out = binding.jacobi_hsvd(torch.from_numpy(G).to(cuda_dev), torch.from_numpy(J).to(cuda_dev), opts,
-                              raise_on_error=False)
+    opts = binding.default_opts(block_w=8, **kw)
+    out = binding.jacobi_hsvd(torch.from_numpy(G).to(dev), torch.from_numpy(J).to(dev), opts, raise_on_error=False)
     torch.cuda.synchronize()
     out = to_np(out)
     assert out["status"] == 0, out["info"]
     compare(G, J, out)
+
+
+def test_split16_complex(cuda_dev):
+    _complex_graded(cuda_dev, **S16)
+
+
+MMA = dict(f64_products="mma")
+
+
+@pytest.mark.parametrize("precision,block_mode", [("fp64", "full"), ("fp64", "oriented"), ("fp32", "oriented")])
+def test_mma_products_config2(cuda_dev, precision, block_mode):
+    from paper_1008_0201_gb300 import inputs
+
+    G, J = inputs.config2_hyperbolic()
+    out = run(G, J, cuda_dev, block_w=32, precision=precision, block_mode=block_mode, **MMA)
+    assert out["status"] == 0, out["info"]
+    compare(G, J, out)
+
+
+@pytest.mark.parametrize("m,n,w,frac", [(130, 100, 16, 0.4), (37, 37, 5, 0.5), (4500, 40, 8, 0.3)])
+def test_mma_products_ragged(cuda_dev, m, n, w, frac):
+    g = np.random.default_rng(5300 + m * 7 + n)
+    G = g.standard_normal((m, n))
+    J = np.ones(n, dtype=np.int8)
+    J[g.choice(n, size=int(round(frac * n)), replace=False)] = -1
+    out = run(G, J, cuda_dev, block_w=w, **MMA)
+    assert out["status"] == 0, out["info"]
+    compare(G, J, out)
+
+
+def test_mma_products_batched_and_complex(cuda_dev):
+    Gs, Js = small_batch(8, salt=22, pd_every=3)
+    outs, rc = run_batched(Gs, Js, cuda_dev, **MMA)
+    assert rc == 0
+    check_all(Gs, Js, outs)
+    _complex_graded(cuda_dev, **MMA)
