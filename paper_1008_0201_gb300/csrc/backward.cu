@@ -9,8 +9,8 @@
 // with F_ij set to 0 where |lambda_i - lambda_j| <= deg_tol max_k |lambda_k| (degenerate pairs:
 // exact only for losses invariant inside a degenerate eigenspace).  Through the factor,
 // H = G J G^T gives G_bar = (H_bar + H_bar^T) G J = 2 H_bar G J (J-adjusted for J != I).
-// The three n x n products run on the FP64 tensor path (k_gemm64), the elementwise middle step
-// and the column signs in the kernels below.
+// The n x n products run as FP64-accurate sums of exact FP16 tensor-core digit products
+// (k_gemm_oz, ozaki.cu), the elementwise middle step and the column signs in the kernels below.
 #include <algorithm>
 #include <cstring>
 
@@ -18,9 +18,9 @@
 #include "jacobi_gb300.h"
 
 namespace jac {
-__global__ void k_gemm64(int Mr, int Nc, int K, const double* A, int lda, int transA, const double* B, int ldb,
-                         const int8_t* sb, const int8_t* dsub, double* C, int ldc, int sym, int transB, long long sa,
-                         long long sbb, long long sc);
+int oz_gemm_launch(int Mr, int Nc, int K, const double* A, int lda, int transA, const double* B, int ldb,
+                   const int8_t* sb, const int8_t* dsub, double* C, int ldc, int sym, int transB, long long sa,
+                   long long sbb, long long sc, int batch, cudaStream_t st);
 
 // In place on M = U^T U_bar (n x n, ld n, problem blockIdx.y at stride sM):
 //   M_ii <- lambda_bar_i,   M_ij, M_ji <- (M_ij - M_ji) / (2 (lambda_j - lambda_i))  (0 if degenerate)
@@ -113,21 +113,19 @@ extern "C" int jacobi_eig_backward(int batch, int n, const double* lambda, long 
   }
   double* M = static_cast<double*>(scratch);
   double* T = M + nn * batch;
-  const dim3 gg((n + 31) / 32, (n + 31) / 32, batch);
+  int rg = 0;
   // M = U^T U_bar
-  if (U_bar)
-    k_gemm64<<<gg, 128, 0, st>>>(n, n, n, U, ldu, 1, U_bar, ldub, nullptr, nullptr, M, n, 0, 0, s_u, s_ubar, nn);
+  if (U_bar) rg |= oz_gemm_launch(n, n, n, U, ldu, 1, U_bar, ldub, nullptr, nullptr, M, n, 0, 0, s_u, s_ubar, nn, batch, st);
   const int eb = (int)std::min<long long>(1024, (nn + 255) / 256);
   k_bwd_mid<<<dim3(eb, batch), 256, 0, st>>>(n, M, nn, lambda, s_lam, lambda_bar, s_lbar, U_bar ? 1 : 0, deg_tol);
-  // T = U K_s, H_bar = T U^T (symmetric: upper tiles, mirrored)
-  k_gemm64<<<gg, 128, 0, st>>>(n, n, n, U, ldu, 0, M, n, nullptr, nullptr, T, n, 0, 0, s_u, nn, nn);
-  k_gemm64<<<gg, 128, 0, st>>>(n, n, n, T, n, 0, U, ldu, nullptr, nullptr, H_bar, ldh, 1, 1, nn, s_u, s_h);
+  // T = U K_s, H_bar = T U^T (symmetric: upper entries, mirrored)
+  rg |= oz_gemm_launch(n, n, n, U, ldu, 0, M, n, nullptr, nullptr, T, n, 0, 0, s_u, nn, nn, batch, st);
+  rg |= oz_gemm_launch(n, n, n, T, n, 0, U, ldu, nullptr, nullptr, H_bar, ldh, 1, 1, nn, s_u, s_h, batch, st);
   if (G_bar) {  // G_bar = 2 H_bar G J
-    k_gemm64<<<gg, 128, 0, st>>>(n, n, n, H_bar, ldh, 0, G, ldg, nullptr, nullptr, G_bar, ldgb, 0, 0, s_h, s_g,
-                                 s_gb);
+    rg |= oz_gemm_launch(n, n, n, H_bar, ldh, 0, G, ldg, nullptr, nullptr, G_bar, ldgb, 0, 0, s_h, s_g, s_gb, batch, st);
     k_scale_cols<<<dim3(eb, batch), 256, 0, st>>>(n, n, G_bar, ldgb, s_gb, J, s_j, 2.0);
   }
-  int status = (cudaGetLastError() == cudaSuccess) ? JAC_OK : JAC_ECUDA;
+  int status = (rg == 0 && cudaGetLastError() == cudaSuccess) ? JAC_OK : JAC_ECUDA;
   cudaFreeAsync(scratch, st);
   return status;
 }

@@ -59,6 +59,9 @@ __global__ void k_gram_oz(const JacProb* probs, int s, int CS);
 __global__ void k_update_oz(const JacProb* probs, int s, int gslabs);
 size_t oz_gram_smem_bytes();
 size_t oz_update_smem_bytes();
+int oz_gemm_launch(int Mr, int Nc, int K, const double* A, int lda, int transA, const double* B, int ldb,
+                   const int8_t* sb, const int8_t* dsub, double* C, int ldc, int sym, int transB, long long sa,
+                   long long sbb, long long sc, int batch, cudaStream_t st);
 }  // namespace jac
 
 using namespace jac;
@@ -535,7 +538,8 @@ int solve_real(int m, int n, int dtype, void* Gv, int ldg, const int8_t* Jdev, c
     ck(cudaGetLastError());
   }
   // the digit-product Gram is ~20x cheaper per row than the FP64 mma one: >= 32 rows per CTA
-  const int CS = choose_cluster(P.half, P.mp, o.f64_products == JAC_F64_SPLIT16 ? 32 : 16),
+  const bool split16 = o.f64_products == JAC_F64_SPLIT16;
+  const int CS = choose_cluster(P.half, P.mp, split16 ? 32 : 16),
             CS32 = choose_cluster(P.half, P.mp, 64);
   const int gslabs = (P.mp + 63) / 64;
   const int tslabs = gslabs + (have_vw ? (P.np + 63) / 64 : 0);
@@ -664,7 +668,12 @@ int solve_real(int m, int n, int dtype, void* Gv, int ldg, const int8_t* Jdev, c
         launches += 1;
         const dim3 gsym((n + 31) / 32, (n + 31) / 32, 1);
         for (int it = 0; it < 4 && status == JAC_OK; ++it) {
-          k_gemm64<<<gsym, 128, 0, st>>>(n, n, n, hp.Vw, P.np, 1, hp.Vw, P.np, Jdev, L.Js, L.Mn, n, 1, 0, 0, 0, 0);
+          if (split16)
+            ck(oz_gemm_launch(n, n, n, hp.Vw, P.np, 1, hp.Vw, P.np, Jdev, L.Js, L.Mn, n, 1, 0, 0, 0, 0, 1, st)
+                   ? cudaErrorLaunchFailure
+                   : cudaSuccess);
+          else
+            k_gemm64<<<gsym, 128, 0, st>>>(n, n, n, hp.Vw, P.np, 1, hp.Vw, P.np, Jdev, L.Js, L.Mn, n, 1, 0, 0, 0, 0);
           ck(cudaMemsetAsync(L.mmax, 0, sizeof(unsigned long long), st));
           k_absmax64<<<std::min(1024, (n * n + 255) / 256), 256, 0, st>>>(n, L.Mn, n, L.mmax);
           unsigned long long hm = 0;
@@ -688,8 +697,13 @@ int solve_real(int m, int n, int dtype, void* Gv, int ldg, const int8_t* Jdev, c
           if (mm * mm + 1e-6 * mm <= 2e-16) break;
         }
         // G_int = G_in V (V rows are input columns): the FP64 factor the polish works on
-        k_gemm64<<<dim3((m + 31) / 32, (n + 31) / 32, 1), 128, 0, st>>>(m, n, n, hio.G, ldg, 0, hp.Vw, P.np, nullptr,
-                                                                        nullptr, hp.Gw, P.mp, 0, 0, 0, 0, 0);
+        if (split16)
+          ck(oz_gemm_launch(m, n, n, hio.G, ldg, 0, hp.Vw, P.np, nullptr, nullptr, hp.Gw, P.mp, 0, 0, 0, 0, 0, 1, st)
+                 ? cudaErrorLaunchFailure
+                 : cudaSuccess);
+        else
+          k_gemm64<<<dim3((m + 31) / 32, (n + 31) / 32, 1), 128, 0, st>>>(m, n, n, hio.G, ldg, 0, hp.Vw, P.np, nullptr,
+                                                                          nullptr, hp.Gw, P.mp, 0, 0, 0, 0, 0);
         ++launches;
         ck(cudaGetLastError());
         ck(cudaStreamSynchronize(st));

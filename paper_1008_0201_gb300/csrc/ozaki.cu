@@ -9,6 +9,8 @@
 // small column of G stays accurate relative to itself: its entries of V~ are small too.
 #include <cooperative_groups.h>
 
+#include <mutex>
+
 #include "jacobi_common.cuh"
 #include "ozaki.cuh"
 
@@ -357,5 +359,210 @@ __global__ void __launch_bounds__(256) k_update_oz(const JacProb* __restrict__ p
 
 size_t oz_gram_smem_bytes() { return sizeof(OzGramSmem); }
 size_t oz_update_smem_bytes() { return sizeof(OzUpdSmem); }
+
+// ------------------------------------------------------------------------------- GEMM
+// C = op(A) diag(sb) op(B) - diag(dsub), the contract of k_gemm64 (dense.cu), from FP16 digit
+// products: column-major, C is Mr x Nc, batch member blockIdx.z at element strides sa, sbb, sc;
+//   transA = 1: op(A)[i][r] = A[i * lda + r], else A[r * lda + i];
+//   transB = 1: op(B)[r][j] = B[r * ldb + j], else B[j * ldb + r];
+//   sb: optional +-1 per r; dsub: optional, its sign subtracted on the diagonal;
+//   sym = 1: C symmetric (Mr == Nc), entries j >= i computed and mirrored.
+// K runs in segments of 256 (4 chunks of 64), each an exact FP32 level sum recombined into FP64.
+// Per segment the scales are those of k_update_oz: c_r = bound exponent of column r of the CTA's
+// op(A) rows, then the rows of op(A) D^-1 and the columns of D op(B) (D = diag(2^c_r)) are the
+// scale groups, so a term is exact to 2^-53 of its own row and column sizes even when the columns
+// of A (or rows of B) are graded.  Grid (ceil(Mr/64), ceil(Nc/32), batch), 256 threads: warp w
+// computes row tile w & 3 (16 rows) and column tiles 2 (w >> 2) + {0, 1}.
+#define OZM_TI 64
+#define OZM_TJ 32
+#define OZM_KC 64
+#define OZM_SEG 256
+#define OZM_P (OZM_KC + 8)
+#define OZM_NL 9
+struct OzGemmSmem {
+  __half A[OZ_T][OZM_TI][OZM_P];  // digits of op(A) D^-1: [t][row][r]
+  __half B[OZ_T][OZM_TJ][OZM_P];  // digits of D op(B): [t][column][r]
+  int ck[OZM_SEG];                // c_r of the segment (0: zero column)
+  int rexp[OZM_TI];
+  int cexp[OZM_TJ];
+};
+
+__global__ void __launch_bounds__(256) k_gemm_oz(int Mr, int Nc, int K, const double* __restrict__ A, int lda,
+                                                int transA, const double* __restrict__ B, int ldb,
+                                                const int8_t* __restrict__ sb, const int8_t* __restrict__ dsub,
+                                                double* __restrict__ C, int ldc, int sym, int transB, long long sa,
+                                                long long sbb, long long sc) {
+  extern __shared__ __align__(16) unsigned char oz_raw[];
+  OzGemmSmem& sm = *reinterpret_cast<OzGemmSmem*>(oz_raw);
+  A += (size_t)blockIdx.z * sa;
+  B += (size_t)blockIdx.z * sbb;
+  C += (size_t)blockIdx.z * sc;
+  const int i0 = blockIdx.x * OZM_TI, j0 = blockIdx.y * OZM_TJ;
+  if (sym && j0 + OZM_TJ - 1 < i0) return;  // no entry with j >= i
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t4 = lane & 3;
+  const int ai = tid >> 2, ar = tid & 3, bj = tid >> 3, br = tid & 7;  // 4 threads per row, 8 per column
+  const bool rowok = i0 + ai < Mr, colok = j0 + bj < Nc;
+  const int ti = warp & 3, tj0 = 2 * (warp >> 2);
+  const int arow = 16 * ti + (lane & 7) + 8 * ((lane >> 3) & 1), akof = 8 * (lane >> 4);
+  const int bcol = 8 * tj0 + (lane & 7) + 8 * (lane >> 4), bkof = 8 * ((lane >> 3) & 1);
+  auto a_at = [&](int i, int r) -> double {  // op(A)[i0 + i][r], in range
+    return transA ? A[(size_t)(i0 + i) * lda + r] : A[(size_t)r * lda + i0 + i];
+  };
+  auto b_at = [&](int j, int r) -> double {  // op(B)[r][j0 + j] with the sign sb_r, in range
+    const double y = transB ? B[(size_t)r * ldb + j0 + j] : B[(size_t)(j0 + j) * ldb + r];
+    return (sb && sb[r] < 0) ? oz_neg_if(y, true) : y;
+  };
+  float acc0[OZM_NL][4], acc1[OZM_NL][4];
+  double res[2][4];
+#pragma unroll
+  for (int h = 0; h < 2; ++h)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) res[h][e] = 0.0;
+  for (int s0 = 0; s0 < K; s0 += OZM_SEG) {
+    const int slen = min(OZM_SEG, K - s0);
+    // ---- c_r: thread tid takes column r = s0 + tid of the CTA's op(A) rows
+    {
+      int c = 0;
+      if (tid < slen) {
+        const int imax = min(OZM_TI, Mr - i0);
+#pragma unroll 16
+        for (int i = 0; i < imax; ++i) c = max(c, oz_bexp(a_at(i, s0 + tid)));
+      }
+      __syncthreads();  // the previous segment's exponents are no longer read
+      sm.ck[tid] = c;
+    }
+    __syncthreads();
+    // ---- row groups of op(A) D^-1 and column groups of D op(B)
+    {
+      int ea = OZ_NO_EXP, eb = OZ_NO_EXP;
+      if (rowok) {
+#pragma unroll 16
+        for (int r = ar; r < slen; r += 4) {
+          const int ex = oz_bexp(a_at(ai, s0 + r));
+          if (ex != 0) ea = max(ea, ex - sm.ck[r]);
+        }
+      }
+      if (colok) {
+#pragma unroll 16
+        for (int r = br; r < slen; r += 8) {
+          const int ex = oz_bexp(b_at(bj, s0 + r)), c = sm.ck[r];
+          if (ex != 0 && c != 0) eb = max(eb, ex + c);
+        }
+      }
+      ea = max(ea, __shfl_xor_sync(0xffffffffu, ea, 1));
+      ea = max(ea, __shfl_xor_sync(0xffffffffu, ea, 2));
+      eb = max(eb, __shfl_xor_sync(0xffffffffu, eb, 1));
+      eb = max(eb, __shfl_xor_sync(0xffffffffu, eb, 2));
+      eb = max(eb, __shfl_xor_sync(0xffffffffu, eb, 4));
+      if (ar == 0) sm.rexp[ai] = ea;
+      if (br == 0) sm.cexp[bj] = eb;
+    }
+    __syncthreads();
+    const int my_ea = sm.rexp[ai], my_eb = sm.cexp[bj];
+#pragma unroll
+    for (int L = 0; L < OZM_NL; ++L)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        acc0[L][e] = 0.0f;
+        acc1[L][e] = 0.0f;
+      }
+    for (int kc = 0; kc < slen; kc += OZM_KC) {
+      // ---- chunk values (all loads first), digits
+      double xa[16], xb[8];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int r = kc + ar + 4 * u;
+        xa[u] = (rowok && r < slen) ? a_at(ai, s0 + r) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int r = kc + br + 8 * u;
+        xb[u] = (colok && r < slen) ? b_at(bj, s0 + r) : 0.0;
+      }
+      __syncthreads();  // the previous chunk's digits are consumed
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int r = kc + ar + 4 * u;
+        __half d[OZ_T];
+        const int c = (r < slen) ? sm.ck[r] : 0;
+        oz_split(oz_fixed(xa[u], oz_bexp(xa[u]) - c - my_ea), d);
+#pragma unroll
+        for (int t = 0; t < OZ_T; ++t) sm.A[t][ai][ar + 4 * u] = d[t];
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int r = kc + br + 8 * u;
+        __half d[OZ_T];
+        const int c = (r < slen) ? sm.ck[r] : 0;
+        oz_split(c != 0 ? oz_fixed(xb[u], oz_bexp(xb[u]) + c - my_eb) : 0ll, d);
+#pragma unroll
+        for (int t = 0; t < OZ_T; ++t) sm.B[t][bj][br + 8 * u] = d[t];
+      }
+      __syncthreads();
+#pragma unroll 1
+      for (int kk = 0; kk < OZM_KC; kk += 16) {
+        unsigned fa[OZ_T][4], fb0[OZ_T][2], fb1[OZ_T][2];
+#pragma unroll
+        for (int t = 0; t < OZ_T; ++t) {
+          unsigned r4[4];
+          oz_ldsm4(fa[t], &sm.A[t][arow][kk + akof]);
+          oz_ldsm4(r4, &sm.B[t][bcol][kk + bkof]);
+          fb0[t][0] = r4[0];
+          fb0[t][1] = r4[1];
+          fb1[t][0] = r4[2];
+          fb1[t][1] = r4[3];
+        }
+        oz_levels(acc0, fa, fb0);
+        oz_levels(acc1, fa, fb1);
+      }
+    }
+    // ---- the segment's exact level sums into FP64
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int il = 16 * ti + g + 8 * (e >> 1);
+      const int jl0 = 8 * tj0 + 2 * t4 + (e & 1), jl1 = jl0 + 8;
+      res[0][e] += oz_value(acc0, e, sm.rexp[il] + sm.cexp[jl0] - 2056);
+      res[1][e] += oz_value(acc1, e, sm.rexp[il] + sm.cexp[jl1] - 2056);
+    }
+  }
+#pragma unroll
+  for (int h = 0; h < 2; ++h)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int i = i0 + 16 * ti + g + 8 * (e >> 1), j = j0 + 8 * (tj0 + h) + 2 * t4 + (e & 1);
+      if (i < Mr && j < Nc && (!sym || j >= i)) {
+        double v = res[h][e];
+        if (dsub && i == j) v -= (dsub[i] < 0) ? -1.0 : 1.0;
+        C[(size_t)j * ldc + i] = v;
+        if (sym && j > i) C[(size_t)i * ldc + j] = v;
+      }
+    }
+}
+
+size_t oz_gemm_smem_bytes() { return sizeof(OzGemmSmem); }
+
+// Launch with the grid of k_gemm_oz; sets the kernel's shared-memory limit on first use per
+// device (outside any stream capture: the solvers call it before capturing).
+int oz_gemm_launch(int Mr, int Nc, int K, const double* A, int lda, int transA, const double* B, int ldb,
+                   const int8_t* sb, const int8_t* dsub, double* C, int ldc, int sym, int transB, long long sa,
+                   long long sbb, long long sc, int batch, cudaStream_t st) {
+  static std::mutex mu;
+  static bool done[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if (!done[dev]) {
+      if (cudaFuncSetAttribute(k_gemm_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(OzGemmSmem)) !=
+          cudaSuccess)
+        return 1;
+      done[dev] = true;
+    }
+  }
+  const dim3 grid((Mr + OZM_TI - 1) / OZM_TI, (Nc + OZM_TJ - 1) / OZM_TJ, batch);
+  k_gemm_oz<<<grid, 256, sizeof(OzGemmSmem), st>>>(Mr, Nc, K, A, lda, transA, B, ldb, sb, dsub, C, ldc, sym, transB,
+                                                    sa, sbb, sc);
+  return cudaGetLastError() == cudaSuccess ? 0 : 1;
+}
 
 }  // namespace jac

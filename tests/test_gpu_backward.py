@@ -183,3 +183,28 @@ def test_backward_full_size_sampled(cuda_dev):
         Hr = oracle.eig_backward(ref["lam"], Ur, w_np, Ubr)
         err = np.linalg.norm(Hb[b] - Hr) / np.linalg.norm(Hr)
         assert err <= 1e-9, (b, err)
+
+
+def test_backward_kernel_vs_oracle_same_inputs(cuda_dev):
+    """The backward kernel alone: the oracle's backward applied to the GPU's own eigenpairs must
+    give the GPU's H_bar to FP64 product accuracy (the n x n products run as FP16 digit products;
+    n = 150 leaves ragged 64 x 32 tiles)."""
+    import torch
+
+    import oracle
+    from paper_1008_0201_gb300 import binding
+
+    g = np.random.default_rng(47)
+    n, batch, k = 150, 2, 5
+    Hs = np.stack([_spd(n, g) for _ in range(batch)])
+    w = torch.from_numpy(g.standard_normal(n)).to(cuda_dev)
+    C = torch.from_numpy(g.standard_normal((n, 3))).to(cuda_dev)
+    lam, U = _forward(Hs, cuda_dev)
+    _, lam_bar, U_bar = _loss_grads(lam, U, w, C, k)
+    Hb, _ = binding.jacobi_eig_backward(lam, U, lam_bar, U_bar)
+    Hb = Hb.cpu().numpy()
+    for b in range(batch):
+        Hr = oracle.eig_backward(lam[b].cpu().numpy(), U[b].cpu().numpy(), lam_bar[b].cpu().numpy(),
+                                 U_bar[b].cpu().numpy())
+        err = np.linalg.norm(Hb[b] - Hr) / np.linalg.norm(Hr)
+        assert err <= 1e-12, err
