@@ -481,10 +481,10 @@ def main():
             fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12  # unit counts x max SM clock
             # DRAM bytes per launch from the ncu capture of this configuration (the summary in
             # profiles/k_pivot_c2_hbsc_ncu.md); other configurations were not captured
-            default_cfg = (args.block_mode, args.ordering, args.factor, args.precision) == \
-                ("oriented", "round_robin", "chol_signpiv", "fp32")
+            default_cfg = (args.block_mode, args.ordering, args.factor, args.precision, args.f64_products) == \
+                ("oriented", "round_robin", "chol_signpiv", "fp32", "split16")
             roof = {"bound": "alu", "achieved": flops / avg_s / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
-                    "frac": flops / avg_s / 1e12 / fp32_peak, "traffic": 337664 if default_cfg else None,
+                    "frac": flops / avg_s / 1e12 / fp32_peak, "traffic": 343552 if default_cfg else None,
                     "kernel": "k_pivot", "peak_source": "FP32 lanes x max clock (152 x 128 x 2 x 2.07 GHz)"}
         else:
             # FP64 mma: gram m k^2, update (m + n) k^2 multiply-adds per pair

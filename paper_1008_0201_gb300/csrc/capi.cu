@@ -537,9 +537,11 @@ int solve_real(int m, int n, int dtype, void* Gv, int ldg, const int8_t* Jdev, c
     ++launches;
     ck(cudaGetLastError());
   }
-  // the digit-product Gram is ~20x cheaper per row than the FP64 mma one: >= 32 rows per CTA
+  // the digit-product Gram is ~20x cheaper per row than the FP64 mma one and holds 173 KB of
+  // shared memory per CTA: >= 64 rows per CTA, so its clusters stay at <= 8 CTAs (clusters of 16
+  // such CTAs ran in two waves on the 512 x 512 workload: 61 us against 25 us of SM time)
   const bool split16 = o.f64_products == JAC_F64_SPLIT16;
-  const int CS = choose_cluster(P.half, P.mp, split16 ? 32 : 16),
+  const int CS = choose_cluster(P.half, P.mp, split16 ? 64 : 16),
             CS32 = choose_cluster(P.half, P.mp, 64);
   const int gslabs = (P.mp + 63) / 64;
   const int tslabs = gslabs + (have_vw ? (P.np + 63) / 64 : 0);
