@@ -314,8 +314,11 @@ void carve_problem(Arena& ar, const Plan& P, JacProb& d, JacIO& io, bool weights
 }
 
 // One launch of the three step kernels for every problem of a class array.
+// fallback = false leaves out the FP64 pivot kernel: blocks the FP32 pivot hands over are then
+// not rotated in this step (the FP32 sweeps of the mixed mode switch to FP64 on a handover).
 int launch_step(JacProb* dprobs, int count, int km, int max_half, int gslabs, int tslabs, int CS, int CS32, int s,
-                bool lowp, const PivotParams& pp, cudaStream_t st, ProfRun& prof, long long& launches) {
+                bool lowp, bool fallback, const PivotParams& pp, cudaStream_t st, ProfRun& prof,
+                long long& launches) {
   int r = 0;
   size_t pm = prof.pre(JAC_KERNEL_GRAM, st);
   if (lowp)
@@ -329,7 +332,7 @@ int launch_step(JacProb* dprobs, int count, int km, int max_half, int gslabs, in
   if (r) return r;
   pm = prof.pre(JAC_KERNEL_PIVOT, st);
   pivot_launch(km, max_half, count, st, dprobs, s, pp);
-  pivot64_launch(km, max_half, count, st, dprobs, s, pp);  // blocks the FP32 kernel handed over
+  if (fallback) pivot64_launch(km, max_half, count, st, dprobs, s, pp);  // blocks the FP32 kernel handed over
   prof.post(pm, st);
   pm = prof.pre(JAC_KERNEL_UPDATE, st);
   if (lowp)
@@ -339,7 +342,7 @@ int launch_step(JacProb* dprobs, int count, int km, int max_half, int gslabs, in
   else
     k_update<<<dim3(max_half, tslabs, count), 128, kUpdSmem, st>>>(dprobs, s, gslabs);
   prof.post(pm, st);
-  launches += 4;
+  launches += fallback ? 4 : 3;
   return cudaGetLastError() == cudaSuccess ? 0 : JAC_ECUDA;
 }
 
@@ -605,7 +608,9 @@ int solve_real(int m, int n, int dtype, void* Gv, int ldg, const int8_t* Jdev, c
     }
     auto record = [&](cudaStream_t ss, long long& nl, ProfRun& pr) -> int {
       for (int s = 0; s < nsteps; ++s)
-        if (int r = launch_step(L.probs, 1, P.km, P.half, gslabs, tslabs, CS, CS32, s, low, pp, ss, pr, nl)) return r;
+        if (int r = launch_step(L.probs, 1, P.km, P.half, gslabs, tslabs, CS, CS32, s, low, phase != 1, pp, ss, pr,
+                                nl))
+          return r;
       k_sweep_reduce<<<1, 256, 0, ss>>>(L.probs, L.io, L.rec, 0, nullptr);
       ++nl;
       return cudaGetLastError() == cudaSuccess ? 0 : JAC_ECUDA;
@@ -639,7 +644,9 @@ int solve_real(int m, int n, int dtype, void* Gv, int ldg, const int8_t* Jdev, c
     ns_total += hrec.ns_steps;
     inner_total += hrec.inner_sweeps;
     for (int u = 0; u < 4; ++u) cyc_total[u] += hrec.cyc[u];
-    bool lowp_singular = false;
+    // a block the FP32 pivot could not factor or J-orthogonalize was handed over (and, in the
+    // FP32 sweeps, left unrotated): the FP64 phase decides it
+    bool lowp_singular = phase == 1 && (hrec.err & JAC_DEVERR_HANDOVER);
     if (hrec.err & JAC_DEVERR_NOTPD) {
       if (phase != 1) {
         status = JAC_ENOTPD;
@@ -1108,8 +1115,8 @@ int solve_batched(int batch, const int* m, const int* n, int dtype, void* const*
       if (cudaMemsetAsync(d_remaining, 0, sizeof(int), ss) != cudaSuccess) return JAC_ECUDA;
       for (auto& c : cls) {
         for (int s = 0; s < c.max_steps; ++s)
-          if (int r = launch_step(c.probs, c.count, c.km, c.max_half, c.gslabs, c.tslabs, 1, 1, s, fp32_only, pp, ss,
-                                  pr, nl))
+          if (int r = launch_step(c.probs, c.count, c.km, c.max_half, c.gslabs, c.tslabs, 1, 1, s, fp32_only, true, pp,
+                                  ss, pr, nl))
             return r;
         k_sweep_reduce<<<c.count, 256, 0, ss>>>(c.probs, c.io, c.rec, 1, d_remaining);
         ++nl;

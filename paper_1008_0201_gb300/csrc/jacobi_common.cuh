@@ -18,6 +18,7 @@
 #define JAC_DEVERR_NOTPD 1u
 #define JAC_DEVERR_INNER_LIMIT 2u
 #define JAC_DEVERR_NONFINITE 4u
+#define JAC_DEVERR_HANDOVER 8u  // a pivot block went to the FP64 pivot kernel (not an error)
 
 namespace jac {
 

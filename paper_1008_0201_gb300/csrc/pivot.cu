@@ -464,6 +464,7 @@ __global__ void __launch_bounds__((KM / 2) * LPP, 1)
   if (sm.bad) {  // handed over to the FP64 pivot kernel, which decides on rank deficiency
     if (tid == 0) {
       a.skip[pair] = 2;
+      atomicOr(err, JAC_DEVERR_HANDOVER);
       st.cyc[0] = t_stats - t_start;
       st.cyc[1] = clock64() - t_stats;
       st.cyc[2] = st.cyc[3] = 0;
@@ -865,6 +866,7 @@ __global__ void __launch_bounds__((KM / 2) * LPP, 1)
   if (!ns_ok) {  // V is not J-unitary to FP64 accuracy after the step budget: FP64 pivot kernel
     if (tid == 0) {
       a.skip[pair] = 2;
+      atomicOr(err, JAC_DEVERR_HANDOVER);
       st.rotations = total_rot;
       st.inner_sweeps = (inner < max_inner) ? inner + 1 : max_inner;
       st.ns_steps = ns;
