@@ -142,7 +142,9 @@ void jacobi_default_opts(jac_opts* opts);
 /* Short text for a return code. */
 const char* jacobi_status_string(int status);
 
-/* Library version, major*10000 + minor*100 + patch. */
+/* Library version, major*10000 + minor*100 + patch.  The minor number changes with the layout of
+ * jac_opts / jac_info (0.3: jac_opts.f64_products). */
+#define JAC_VERSION 300
 int jacobi_version(void);
 
 /*

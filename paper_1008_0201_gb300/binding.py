@@ -20,6 +20,7 @@ FACTOR = {"chol": 0, "chol_diagpiv": 1, "chol_signpiv": 2}
 PRECISION = {"fp64": 0, "fp32": 1, "fp32_only": 2}
 BLOCK_MODE = {"full": 0, "oriented": 1}
 F64_PRODUCTS = {"mma": 0, "split16": 1}
+ABI_VERSION = 300  # JAC_VERSION of include/jacobi_gb300.h whose structs JacOpts / JacInfo mirror
 
 
 class JacOpts(ctypes.Structure):
@@ -77,6 +78,9 @@ def load_library(path=LIB_PATH):
     lib.jacobi_status_string.restype = ctypes.c_char_p
     lib.jacobi_version.argtypes = []
     lib.jacobi_version.restype = I
+    if lib.jacobi_version() // 100 != ABI_VERSION // 100:  # JacOpts / JacInfo mirror this layout
+        raise ImportError("libjacobi_gb300.so is version %d, the binding expects %d: rebuild it"
+                          % (lib.jacobi_version(), ABI_VERSION))
     lib.jacobi_hsvd.argtypes = [I, I, I, P, I, P, ctypes.POINTER(JacOpts), P, P, I, P, I, ctypes.POINTER(JacInfo), P]
     lib.jacobi_hsvd.restype = I
     lib.jacobi_eig_pd.argtypes = [I, I, I, P, I, ctypes.POINTER(JacOpts), P, P, I, P, I, ctypes.POINTER(JacInfo), P]

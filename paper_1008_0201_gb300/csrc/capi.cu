@@ -1219,7 +1219,7 @@ const char* jacobi_status_string(int s) {
   }
 }
 
-int jacobi_version(void) { return 200; }
+int jacobi_version(void) { return JAC_VERSION; }
 
 int jacobi_profile_begin(int mask) {
   if (mask < 0 || mask >= (1 << JAC_KERNEL_COUNT)) return -1;
