@@ -83,7 +83,8 @@ enum jac_factor {
 
 /* Arithmetic of the sweeps (FP64 and FP32 return FP64-accurate results). */
 enum jac_precision {
-  JAC_PREC_FP64 = 0, /* every sweep: Gram, update and J-orthogonalization of V_P in FP64 (mma f64) */
+  JAC_PREC_FP64 = 0, /* every sweep: Gram, update and J-orthogonalization of V_P FP64-accurate
+                        (products per opts->f64_products) */
   JAC_PREC_FP32 = 1, /* sweeps on an FP32 copy of G with FP32 Gram/update products until the scaled
                         off-norm reaches what FP32 resolves, then V is made J-unitary in FP64,
                         G = G_in V, and FP64 sweeps polish to tol (the outer iteration is
