@@ -230,6 +230,8 @@ int jacobi_eig_batched(int batch, const int* m, const int* n, int dtype, void* c
  *     a degenerate eigenspace);
  * and, through the factor, G_bar = (H_bar + H_bar^T) G J = 2 H_bar G J.
  * A batch of problems of one order n at fixed element strides; all arrays device, column-major.
+ * The n x n products are FP64-accurate sums of exact FP16 digit products (each term exact to
+ * ~2^-53 of its own row and column scale).
  *  1 batch          0 <= batch <= 65535
  *  2 n              order, 1 <= n <= 20000
  *  3 lambda, 4 s_lam            eigenvalues (as returned, ascending), problem b at lambda + b s_lam
