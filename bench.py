@@ -479,8 +479,8 @@ def main():
             rot_per_launch = infos[-1]["rotations"] / max(1, d_n)  # the solve the events bracketed
             flops = rot_per_launch * 18 * k
             fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12  # unit counts x max SM clock
-            # DRAM bytes per launch from the ncu capture of this configuration (the summary in
-            # profiles/k_pivot_c2_hbsc_ncu.md); other configurations were not captured
+            # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu
+            # capture of this configuration's k_pivot; other configurations were not captured
             default_cfg = (args.block_mode, args.ordering, args.factor, args.precision, args.f64_products) == \
                 ("oriented", "round_robin", "chol_signpiv", "fp32", "split16")
             roof = {"bound": "alu", "achieved": flops / avg_s / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",

@@ -23,7 +23,7 @@
  *   The pivot order is the row-cyclic one, (0,1),(0,2),...,(0,n-1),(1,2),...: the inner
  *   strategy for which the paper's convergence argument holds (Sec. 2.4).
  *
- * Readings where the paper is silent (each also listed in the design doc):
+ * Readings where the paper is silent:
  *   - Rotation formulas.  The paper cites them but does not print them.  Writing
  *     b = a_ij = g_i^* g_j = |b| e^{i alpha}:
  *       trig:  zeta = (a_jj - a_ii) / (2|b|),  t = tan(phi) = sign(zeta)/(|zeta| + sqrt(1+zeta^2)),
