@@ -204,7 +204,7 @@ int compute_nb(int n, int w) {
   return nb;
 }
 
-// CTAs per pivot block of the Gram kernels (a cluster splitting the rows): the FP64 Gram is
+// CTAs per pivot block of the Gram kernels (a cluster splitting the rows): the FP64 mma Gram is
 // bound by the FP64 mma rate and takes every SM it can (>= 16 rows per CTA); the FP32 Gram is
 // ~64x cheaper per row, so its CTAs keep >= 64 rows and the cluster reduction stays short
 // (measured on the 512 x 512 workload: 64 rows per CTA beat 32, 128, 256 and 512).

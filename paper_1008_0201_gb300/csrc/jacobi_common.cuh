@@ -1,9 +1,11 @@
 // jacobi_common.cuh -- shared device helpers and internal types of the GB300 Jacobi library.
 //
 // Arithmetic placement on GB300 (measured on the target: FP64 FFMA ~1.0 TFLOP/s, mma.sync
-// m16n8k16 f64 ~1.0 TFLOP/s, FP32 FFMA ~74 TFLOP/s, FP64 sqrt/div ~650 cycles latency):
-//   - every FP64 contraction (pivot Gram block, block update, J-orthogonalization of V_P)
-//     runs on the FP64 tensor path, mma.sync.m16n8k16.f64;
+// m16n8k16 f64 ~1.0 TFLOP/s, FP16 mma.sync ~600 TFLOP/s, FP32 FFMA ~74 TFLOP/s, FP64 sqrt/div
+// ~650 cycles latency):
+//   - every FP64 contraction (pivot Gram block, block update, J-orthogonality residual of V_P)
+//     is an FP64-accurate sum of exact FP16 tensor-core digit products (ozaki.cuh), or, when
+//     selected, runs on the FP64 tensor path, mma.sync.m16n8k16.f64;
 //   - the 2x2 rotation angles are computed in FP32 on a shifted representation that keeps
 //     relative precision near convergence; FP64 enters them only through A_P.
 #pragma once

@@ -23,8 +23,8 @@
 // is applied to G in FP64 must be J-unitary in FP64; it is corrected by Newton-Schulz,
 //     V <- V - V J (V^T J V - J) / 2   (quadratic),
 // whose residual M = V^T J V - J is formed in FP32 from the small Wd when max|Wd| <= 2^-20 and
-// otherwise on the FP64 mma path (symmetric tiles only); the correction product itself is small
-// and is formed in FP32.
+// otherwise from FP16 digit products of Wd (oz_residual) or on the FP64 mma path (symmetric
+// tiles only); the correction product itself is small and is formed in FP32.
 #include "jacobi_common.cuh"
 #include "ozaki.cuh"
 
