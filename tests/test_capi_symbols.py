@@ -60,3 +60,36 @@ def test_library_is_sm103a_only(lib_built):
 
     assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
     assert os.path.exists(build.LIB)
+
+
+def test_opts_layout_matches_header(lib_built):
+    """jacobi_default_opts writes exactly the bytes of the ctypes mirror (no more), and its last
+    field lands where the mirror expects it: the binding's JacOpts has the header's layout."""
+    from paper_1008_0201_gb300 import binding
+
+    lib = binding.load_library()
+    n = ctypes.sizeof(binding.JacOpts)
+    buf = (ctypes.c_ubyte * (n + 64))(*([0xA5] * (n + 64)))
+    lib.jacobi_default_opts(ctypes.cast(buf, ctypes.POINTER(binding.JacOpts)))
+    assert bytes(buf[n:]) == b"\xa5" * 64
+    o = binding.JacOpts.from_buffer_copy(bytes(buf[:n]))
+    assert o.f64_products == binding.F64_PRODUCTS["split16"]
+    assert o.precision == binding.PRECISION["fp64"] and o.tol == 0.0
+    assert lib.jacobi_version() == binding.ABI_VERSION
+
+
+def test_info_layout_matches_header(lib_built):
+    """An argument error returns before any CUDA call, after clearing *info: the cleared bytes are
+    exactly the ctypes mirror's, and the status lands in its field."""
+    from paper_1008_0201_gb300 import binding
+
+    lib = binding.load_library()
+    n = ctypes.sizeof(binding.JacInfo)
+    buf = (ctypes.c_ubyte * (n + 64))(*([0xA5] * (n + 64)))
+    info = ctypes.cast(buf, ctypes.POINTER(binding.JacInfo))
+    rc = lib.jacobi_hsvd(0, 1, 0, None, 1, None, None, None, None, 0, None, 0, info, None)
+    assert rc == -1
+    assert bytes(buf[n:]) == b"\xa5" * 64
+    got = binding.JacInfo.from_buffer_copy(bytes(buf[:n]))
+    assert got.status == -1 and got.sweeps == 0 and got.launches == 0
+    assert all(v == 0.0 for v in got.sweep_ms) and all(v == 0.0 for v in got.sweep_max_scaled)
