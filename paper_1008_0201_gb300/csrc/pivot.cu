@@ -668,33 +668,36 @@ __global__ void __launch_bounds__((KM / 2) * LPP, 1)
           const bool ring = st_ < g - 1;
           const bool give_res = !ring && pos >= g / 2;  // second half of a split sends its resident
           const int dst = ring ? base + ((pos + 1) & (g - 1)) : (pos < g / 2 ? slot + g / 2 : slot - g / 2);
-          float* box = sm.mb[buf] + dst * MBS + l * R;
+          // row l * R + u of a column sits at u * LPP + l of its mailbox slot: the 8 lanes of a
+          // slot write 32 consecutive bytes per u, and the 4 slots of a warp land on distinct
+          // banks (lane-contiguous rows l * R + u put lanes l and l + 4 on the same banks)
+          float* box = sm.mb[buf] + dst * MBS + l;
 #pragma unroll
           for (int u = 0; u < R; ++u) {
-            box[u] = give_res ? fi[u] : fj[u];
-            box[KM + u] = give_res ? wi[u] : wj[u];
+            box[u * LPP] = give_res ? fi[u] : fj[u];
+            box[KM + u * LPP] = give_res ? wi[u] : wj[u];
           }
           if (l == 0) {
             sm.mphys[buf][dst] = give_res ? ci : cj;
             sm.mcn[buf][dst] = give_res ? cni : cnj;
           }
           __syncthreads();
-          const float* in = sm.mb[buf] + slot * MBS + l * R;
+          const float* in = sm.mb[buf] + slot * MBS + l;
           const int cin = sm.mphys[buf][slot];
           const float cnin = sm.mcn[buf][slot];
           if (give_res) {
 #pragma unroll
             for (int u = 0; u < R; ++u) {
-              fi[u] = in[u];
-              wi[u] = in[KM + u];
+              fi[u] = in[u * LPP];
+              wi[u] = in[KM + u * LPP];
             }
             ci = cin;
             cni = cnin;
           } else {
 #pragma unroll
             for (int u = 0; u < R; ++u) {
-              fj[u] = in[u];
-              wj[u] = in[KM + u];
+              fj[u] = in[u * LPP];
+              wj[u] = in[KM + u * LPP];
             }
             cj = cin;
             cnj = cnin;
