@@ -1,6 +1,7 @@
-// ozaki.cu -- the FP64 Gram (Eq. (3.4)) and update (Algorithm 3.4) of a step from exact FP16
+// ozaki.cu -- the FP64 Gram (Eq. (3.4)) and update (Algorithm 3.4) of a step, and a batched
+// GEMM (the precision switch's V^T J V and G_in V, the backward's products), from exact FP16
 // tensor-core digit products (ozaki.cuh).  Same grids, work split and results as k_gram /
-// k_update (gram_update.cu), to FP64 accuracy.
+// k_update (gram_update.cu) and k_gemm64 (dense.cu), to FP64 accuracy.
 //
 // Scale groups.  Gram X^T X: the columns of X over a stage of rows (each column is one row of
 // A = X^T and one column of B = X).  Update Y = X V_P: the columns of X are first brought to a
