@@ -169,3 +169,57 @@ def test_update_without_column_scaling_loses_graded_columns():
     exact = sum(Fraction(a) * Fraction(b) for a, b in zip(x, v))
     scale = sum(abs(Fraction(a) * Fraction(b)) for a, b in zip(x, v))
     assert float(abs(Fraction(got) - exact) / scale) > 1e-12
+
+
+NO_EXP = -100000
+
+
+def update_slab(X, V, nl=9):
+    """Y = X V with the update kernel's scale groups: c_k over the slab's rows, row groups of
+    X D^-1 and column groups of D V over k with c_k > 0; zero rows / columns give OZ_NO_EXP."""
+    rows, K, cols = len(X), len(X[0]), len(V[0])
+    cexp = [max(bexp(X[r][k]) for r in range(rows)) for k in range(K)]
+    rexp = []
+    for r in range(rows):
+        m = [bexp(X[r][k]) - cexp[k] for k in range(K) if bexp(X[r][k]) != 0]
+        rexp.append(max(m) if m else NO_EXP)
+    vexp = []
+    for c in range(cols):
+        m = [bexp(V[k][c]) + cexp[k] for k in range(K) if bexp(V[k][c]) != 0 and cexp[k] != 0]
+        vexp.append(max(m) if m else NO_EXP)
+    Y = [[0.0] * cols for _ in range(rows)]
+    for r in range(rows):
+        for c in range(cols):
+            acc = [0] * nl
+            for k in range(K):
+                x, v = X[r][k], V[k][c]
+                a = fixed(x, bexp(x) - cexp[k] - rexp[r]) if bexp(x) else 0
+                b = fixed(v, bexp(v) + cexp[k] - vexp[c]) if (bexp(v) and cexp[k]) else 0
+                lv = levels(split(a), split(b), nl)
+                acc = [p + q for p, q in zip(acc, lv)]
+            Y[r][c] = value(acc, rexp[r] + vexp[c] - 2056) if any(acc) else 0.0
+    return Y
+
+
+def test_update_zero_rows_columns_and_subnormals():
+    g = random.Random(11)
+    K = 16
+    X = [[g.gauss(0, 1) for _ in range(K)] for _ in range(5)]
+    for r in range(5):
+        X[r][3] = 0.0            # a zero column of the slab (c_k = 0)
+    X[2] = [0.0] * K             # a zero row
+    X[4][7] = 5e-320             # a subnormal entry: treated as zero
+    V = [[g.gauss(0, 1) for _ in range(4)] for _ in range(K)]
+    for k in range(K):
+        V[k][1] = 0.0            # a zero column of V_P
+    V[3][2] = 1e300              # large, but on the zero column of X
+    Y = update_slab(X, V)
+    for r in range(5):
+        for c in range(4):
+            xs = [0.0 if bexp(x) == 0 else x for x in X[r]]
+            exact = sum(Fraction(xs[k]) * Fraction(V[k][c]) for k in range(K))
+            scale = sum(abs(Fraction(xs[k]) * Fraction(V[k][c])) for k in range(K))
+            if scale == 0:
+                assert Y[r][c] == 0.0
+            else:
+                assert abs(Fraction(Y[r][c]) - exact) <= 2 * Fraction(1, 2 ** 53) * scale
