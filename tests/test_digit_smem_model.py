@@ -85,3 +85,28 @@ def test_pivot_residual(KM, KP):
             check(ldsm_rows_B2(tj, kk), KM, P, KM)
             r0 = kk + 2 * 3  # largest J index read for the sign masks: r0 + 9 < KP
             assert r0 + 9 < KP
+
+
+@pytest.mark.parametrize("mp", [16, 48, 512, 1008, 4512, 8192])
+@pytest.mark.parametrize("CS", [1, 2, 4, 8, 16])
+def test_gram_row_split_and_loads(mp, CS):
+    """k_gram_oz's row split over a cluster (rows per CTA rounded up to 16, 128-row stages): the
+    CTAs' ranges tile [0, mp) exactly, every stage is a multiple of 16 rows, and every double2
+    load (rows 64 i + 2 lane, 2 lane + 1 of a stage) is 16-byte aligned and inside the stage."""
+    rpc = ((mp // CS + 15) // 16) * 16
+    covered = []
+    for crank in range(CS):
+        rb = min(mp, crank * rpc)
+        re = min(mp, rb + rpc)
+        r0 = rb
+        while r0 < re:
+            rs = min(128, re - r0)
+            assert rs % 16 == 0 and r0 % 16 == 0
+            for i in range(2):
+                for lane in range(32):
+                    r = 64 * i + 2 * lane
+                    if r < rs:
+                        assert r + 1 < rs and (r0 + r) % 2 == 0  # double2 from a 16-byte aligned column
+            covered.extend(range(r0, r0 + rs))
+            r0 += 128
+    assert covered == list(range(mp))
