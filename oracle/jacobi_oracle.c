@@ -45,7 +45,10 @@
  * weight) are pinned by exhaustive enumeration.  The eigendecomposition adjoint
  * (oracle_eig_backward, no counterpart in the paper) is pinned by the Hellmann-Feynman
  * eigenvalue derivatives, the closed form on diagonal H and central finite differences of a
- * loss on eigenvalues and eigenvectors with LAPACK as the forward map.
+ * loss on eigenvalues and eigenvectors with LAPACK as the forward map.  The three
+ * wide-precision checks (oracle_check_*) are pinned by hand-worked closed forms with nonzero
+ * answers and by exact rational evaluations of their definitions on integer and
+ * Gaussian-integer matrices (tests/test_oracle_checkers.py).
  *
  * Precision: IEEE double throughout the method; the check routines accumulate in long double
  * (80-bit on x86-64, binary128 on aarch64).  Compile with -ffp-contract=off so that results
@@ -66,7 +69,13 @@
  * 3: complex phase not conjugated in g_i'.
  * 4: eigenvalue sign j_k dropped.
  * 5: V accumulation skipped on the second column of each pair.
- * 6: adjoint formed with (U_bar^T U) in place of (U^T U_bar).                            */
+ * 6: adjoint formed with (U_bar^T U) in place of (U^T U_bar).
+ * 7: off-norm check counts each off-diagonal pair once (the factor 2 of a_ij, a_ji dropped).
+ * 8: off-norm check drops the imaginary part of a complex g_i^* g_j.
+ * 9: J-unitarity check signs the rows of V with J_col instead of J_row.
+ * 10: J-unitarity check leaves out the off-diagonal entries of V^* J V - J.
+ * 11: factor residual check multiplies by V^T instead of V.
+ * 12: factor residual check normalizes by ||G||_F instead of ||G0||_F.                    */
 static int g_mutation = 0;
 void oracle_set_mutation(int k) { g_mutation = k; }
 int oracle_get_mutation(void) { return g_mutation; }
@@ -469,8 +478,9 @@ void oracle_check_offdiag(int m, int n, int cplx, const double* G, int ldg, doub
           si += xr * yi - xi * yr;
         }
       }
+      if (g_mutation == 8) si = 0;
       wide b2 = sr * sr + si * si;
-      off2 += 2 * b2;
+      off2 += (g_mutation == 7) ? b2 : 2 * b2;
       wide den = dg[i] * dg[j];
       if (den > 0) {
         wide sc = b2 / den;
@@ -495,7 +505,7 @@ double oracle_check_vjv(int n, int cplx, const double* V, int ldv, const int8_t*
       const double* vj = V + (size_t)j * ldv * es;
       wide sr = 0, si = 0;
       for (int r = 0; r < n; ++r) {
-        wide jr = (J[r] < 0) ? -1.0L : 1.0L;
+        wide jr = (((g_mutation == 9) ? Jc[r] : J[r]) < 0) ? -1.0L : 1.0L;
         if (!cplx) {
           sr += jr * vi[r] * vj[r];
         } else {
@@ -506,6 +516,7 @@ double oracle_check_vjv(int n, int cplx, const double* V, int ldv, const int8_t*
       }
       if (i == j) sr -= (Jc[i] < 0) ? -1.0L : 1.0L;
       wide e2 = sr * sr + si * si;
+      if (g_mutation == 10 && i != j) e2 = 0;
       acc += (i == j) ? e2 : 2 * e2;
     }
   }
@@ -521,11 +532,12 @@ double oracle_check_factor_residual(int m, int n, int cplx, const double* G0, in
     for (int r = 0; r < m; ++r) {
       wide sr = 0, si = 0;
       for (int k = 0; k < n; ++k) {
+        const size_t vk = (g_mutation == 11) ? (size_t)k * ldv + c : (size_t)c * ldv + k;
         if (!cplx) {
-          sr += (wide)G0[(size_t)k * ldg0 + r] * V[(size_t)c * ldv + k];
+          sr += (wide)G0[(size_t)k * ldg0 + r] * V[vk];
         } else {
           wide ar = G0[((size_t)k * ldg0 + r) * 2], ai = G0[((size_t)k * ldg0 + r) * 2 + 1];
-          wide br = V[((size_t)c * ldv + k) * 2], bi = V[((size_t)c * ldv + k) * 2 + 1];
+          wide br = V[vk * 2], bi = V[vk * 2 + 1];
           sr += ar * br - ai * bi;
           si += ar * bi + ai * br;
         }
@@ -541,7 +553,7 @@ double oracle_check_factor_residual(int m, int n, int cplx, const double* G0, in
   }
   for (int c = 0; c < n; ++c)
     for (int r = 0; r < m * es; ++r) {
-      wide v = G0[(size_t)c * ldg0 * es + r];
+      wide v = (g_mutation == 12) ? G[(size_t)c * ldg * es + r] : G0[(size_t)c * ldg0 * es + r];
       den += v * v;
     }
   return (den > 0) ? (double)sqrtl(num / den) : 0.0;
