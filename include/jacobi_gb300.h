@@ -61,8 +61,14 @@ enum jac_ordering {
   JAC_ORDER_ROUND_ROBIN = 2,  /* circle method: nb-1 perfect matchings */
   JAC_ORDER_CYCLE_WEIGHT = 3  /* per cycle: pairs by descending ||G_p^* G_q||_F^2 /
                                  (||G_p||_F^2 ||G_q||_F^2), greedily packed into steps;
-                                 every pair once per cycle */
+                                 every pair once per cycle.  At most JAC_CYCLE_WEIGHT_MAX_NB
+                                 blocks: a solve whose partition has more blocks is rejected
+                                 as an invalid opts argument */
 };
+
+/* Largest block count of the per-cycle weight ordering (its greedy packing scans every
+ * remaining pair once per step, O(nb^3) work in one CTA per cycle). */
+#define JAC_CYCLE_WEIGHT_MAX_NB 512
 
 /* Pivot block processing (Sec. 2.2). */
 enum jac_block_mode {
@@ -273,11 +279,15 @@ int jacobi_autotune_batched(int count, int precision, int* rules, jac_stream_t s
 
 /*
  * jacobi_sched_pairs -- the device scheduler on its own (Sec. 2.4), for inspection and tests.
- * Writes the block pairs of every step of one cycle for nb blocks (nb even, 2 <= nb <= 4096).
+ * Writes the block pairs of every step of one cycle for nb blocks (nb even, 2 <= nb <= 4096;
+ * nb <= JAC_CYCLE_WEIGHT_MAX_NB for the weight ordering, else -1).
  *  1 nb
  *  2 ordering      enum jac_ordering
  *  3 weights       device double[nb*nb] (row p, column q, q > p used) for
- *                  JAC_ORDER_CYCLE_WEIGHT, else ignored (may be NULL)
+ *                  JAC_ORDER_CYCLE_WEIGHT, else ignored (may be NULL).  Pairs are ranked by
+ *                  descending weight, ties (and equal weights) in enumeration order (p, then
+ *                  q); a NaN weight ranks after every other value, so any weights give a
+ *                  schedule that covers every pair exactly once.
  *  4 pairs         device int[max_steps * (nb/2) * 2]: pairs[(s*(nb/2) + slot)*2 + {0,1}],
  *                  p < q; unused slots are set to -1
  *  5 counts        device int[max_steps]: pairs in step s

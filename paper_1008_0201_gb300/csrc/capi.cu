@@ -20,8 +20,8 @@
 
 namespace jac {
 __global__ void k_sched_static(int nb, int ordering, int nsteps, int* pairs, int* counts);
-__global__ void k_sched_cycle_weight(int nb, const double* w, int* order_g, int* pairs, int* counts, int max_steps,
-                                     int* nsteps_out);
+__global__ void k_sched_rank(int nb, const double* w, int* order);
+__global__ void k_sched_cycle_weight(int nb, int* order, int* pairs, int* counts, int max_steps, int* nsteps_out);
 __global__ void k_block_weights32(const float* G32, int mp, int nb, const int* boff, double* w);
 __global__ void k_gram(const JacProb* probs, int s, int CS);
 __global__ void k_update(const JacProb* probs, int s, int gslabs);
@@ -434,6 +434,8 @@ int solve_real(int m, int n, int dtype, void* Gv, int ldg, const int8_t* Jdev, c
   if (ldg < m) return fail_arg(ap.ldg);
   if (ap.J && !Jdev) return fail_arg(ap.J);
   if (int r = check_opts(o, ap.opts, false)) return fail_arg(-r);
+  if (o.ordering == JAC_ORDER_CYCLE_WEIGHT && compute_nb(n, o.block_w) > JAC_CYCLE_WEIGHT_MAX_NB)
+    return fail_arg(ap.opts);
   if (!lambda) return fail_arg(ap.lambda);
   if (Uv && ldu < m) return fail_arg(ap.ldu);
   if (Uv && Uv == Gv) return fail_arg(ap.U);
@@ -594,9 +596,10 @@ int solve_real(int m, int n, int dtype, void* Gv, int ldg, const int8_t* Jdev, c
       }
       int* nsteps_dev = reinterpret_cast<int*>(reinterpret_cast<char*>(L.probs) + offsetof(JacProb, nsteps));
       k_block_weights32<<<npairs, 256, 0, st>>>(hp.G32, P.mp, P.nb, boff_dev, L.weights);
-      k_sched_cycle_weight<<<1, 1024, sizeof(int) * P.nb, st>>>(P.nb, L.weights, L.order, L.pairs, L.counts,
-                                                                P.nsteps, nsteps_dev);
-      launches += 2;
+      k_sched_rank<<<(npairs + 255) / 256, 256, sizeof(double) * P.nb, st>>>(P.nb, L.weights, L.order);
+      k_sched_cycle_weight<<<1, 1024, sizeof(int) * P.nb, st>>>(P.nb, L.order, L.pairs, L.counts, P.nsteps,
+                                                                nsteps_dev);
+      launches += 3;
       ck(cudaGetLastError());
       ck(cudaMemcpyAsync(&nsteps, nsteps_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
       ck(cudaStreamSynchronize(st));
@@ -790,6 +793,8 @@ int solve_complex(int m, int n, void* Gv, int ldg, const int8_t* Jdev, const jac
   if (ldg < m) return fail_arg(ap.ldg);
   if (ap.J && !Jdev) return fail_arg(ap.J);
   if (int r = check_opts(o, ap.opts, false)) return fail_arg(-r);
+  if (o.ordering == JAC_ORDER_CYCLE_WEIGHT && compute_nb(2 * n, o.block_w) > JAC_CYCLE_WEIGHT_MAX_NB)
+    return fail_arg(ap.opts);
   if (!lambda) return fail_arg(ap.lambda);
   if (Uv && ldu < m) return fail_arg(ap.ldu);
   if (Uv && Uv == Gv) return fail_arg(ap.U);
@@ -1386,6 +1391,7 @@ int jacobi_sched_pairs(int nb, int ordering, const double* weights, int* pairs, 
                        int* nsteps, jac_stream_t stream) {
   cudaStream_t st = (cudaStream_t)stream;
   if (nb < 2 || nb > 4096 || (nb & 1)) return -1;
+  if (ordering == JAC_ORDER_CYCLE_WEIGHT && nb > JAC_CYCLE_WEIGHT_MAX_NB) return -1;
   if (ordering < 0 || ordering > 3) return -2;
   if (ordering == JAC_ORDER_CYCLE_WEIGHT && !weights) return -3;
   if (!pairs) return -4;
@@ -1404,7 +1410,8 @@ int jacobi_sched_pairs(int nb, int ordering, const double* weights, int* pairs, 
   if (cudaMallocAsync(&scratch, sizeof(int) * (npairs + 1), st) != cudaSuccess) return JAC_ENOMEM;
   int* order = static_cast<int*>(scratch);
   int* dn = order + npairs;
-  k_sched_cycle_weight<<<1, 1024, sizeof(int) * nb, st>>>(nb, weights, order, pairs, counts, max_steps, dn);
+  k_sched_rank<<<(npairs + 255) / 256, 256, sizeof(double) * nb, st>>>(nb, weights, order);
+  k_sched_cycle_weight<<<1, 1024, sizeof(int) * nb, st>>>(nb, order, pairs, counts, max_steps, dn);
   int status = (cudaGetLastError() == cudaSuccess) ? JAC_OK : JAC_ECUDA;
   int h = -1;
   if (cudaMemcpyAsync(&h, dn, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) status = JAC_ECUDA;

@@ -94,35 +94,51 @@ __global__ void k_sched_static(int nb, int ordering, int nsteps, int* pairs, int
 // Per-cycle largest-weight ordering: sort all pairs p < q by descending weight w[p*nb+q]
 // (ties: enumeration order p, then q), then fill steps greedily in that order with pairs
 // disjoint from those already in the step, until every pair is scheduled once.
-// One CTA.  order[] (npairs ints) and the busy mask live in dynamic shared memory, so
-// nb*(nb-1)/2 + nb ints must fit (nb <= 128 here; larger nb use the global scratch variant).
-__global__ void k_sched_cycle_weight(int nb, const double* __restrict__ w, int* order_g, int* pairs,
-                                     int* counts, int max_steps, int* nsteps_out) {
-  extern __shared__ int sh_sched[];
+//
+// Ranking: k_sched_rank gives pair x the number of pairs y that precede it, y before x iff
+// key(w_y) > key(w_x) or (key(w_y) == key(w_x) and y < x), with key(v) = v except that a NaN
+// ranks last (key -inf).  This is a total order on (key, id), so the ranks are a permutation
+// of 0..npairs-1 whatever the weights hold.  Grid ceil(npairs / 256) x 256 threads, one pair
+// per thread; the weight matrix is staged row by row in shared memory (nb doubles).
+__device__ __forceinline__ double rank_key(double v) {
+  return (v == v) ? v : -__longlong_as_double(0x7ff0000000000000ll);
+}
+
+__global__ void __launch_bounds__(256) k_sched_rank(int nb, const double* __restrict__ w, int* __restrict__ order) {
+  extern __shared__ double sh_row[];  // [nb]
   const int npairs = nb * (nb - 1) / 2;
-  const int half = nb / 2;
-  int* order = order_g;  // global scratch [npairs]: rank -> pair id
-  int* busy = sh_sched;  // [nb]
-  // pair id x <-> (p, q) in enumeration order
-  // 1. rank each pair: number of pairs that come before it in the sorted order
-  for (int x = threadIdx.x; x < npairs; x += blockDim.x) {
-    // decode x -> (p, q)
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  double kx = 0.0;
+  if (x < npairs) {
     int p = 0, rem = x;
     while (rem >= nb - 1 - p) {
       rem -= nb - 1 - p;
       ++p;
     }
-    int q = p + 1 + rem;
-    double wx = w[p * nb + q];
-    int rank = 0;
-    int y = 0;
-    for (int pp = 0; pp < nb; ++pp)
-      for (int qq = pp + 1; qq < nb; ++qq, ++y) {
-        double wy = w[pp * nb + qq];
-        rank += (wy > wx || (wy == wx && y < x)) ? 1 : 0;
-      }
-    order[rank] = x;
+    kx = rank_key(w[(size_t)p * nb + p + 1 + rem]);
   }
+  int rank = 0, y = 0;
+  for (int pp = 0; pp + 1 < nb; ++pp) {
+    __syncthreads();
+    for (int qq = pp + 1 + threadIdx.x; qq < nb; qq += blockDim.x) sh_row[qq] = rank_key(w[(size_t)pp * nb + qq]);
+    __syncthreads();
+    if (x < npairs)
+      for (int qq = pp + 1; qq < nb; ++qq, ++y) {
+        const double ky = sh_row[qq];
+        rank += (ky > kx || (ky == kx && y < x)) ? 1 : 0;
+      }
+  }
+  if (x < npairs) order[rank] = x;
+}
+
+// Greedy packing of the ranked pairs (one CTA; order[] from k_sched_rank).  order[] is
+// caller-provided global scratch of npairs ints (rank -> pair id, entries marked done in
+// place); only the busy mask (nb ints) is in dynamic shared memory.
+__global__ void k_sched_cycle_weight(int nb, int* order, int* pairs, int* counts, int max_steps, int* nsteps_out) {
+  extern __shared__ int sh_sched[];
+  const int npairs = nb * (nb - 1) / 2;
+  const int half = nb / 2;
+  int* busy = sh_sched;  // [nb]
   for (int i = threadIdx.x; i < max_steps * half; i += blockDim.x) {
     pairs[i * 2] = -1;
     pairs[i * 2 + 1] = -1;
@@ -250,7 +266,11 @@ __global__ void k_block_weights32(const float* __restrict__ G32, int mp, int nb,
     float ff = 0.f;
     for (int u = 0; u < 8; ++u) ff += red[u][0];
     const double den = (double)red[0][1] * (double)red[1][2];
-    w[p * nb + q] = (den > 0.0) ? (double)ff / den : 0.0;
+    double wv = (den > 0.0) ? (double)ff / den : 0.0;
+    // by Cauchy-Schwarz the weight lies in [0, 1]; FP32 norms that overflowed give inf / inf:
+    // such a pair is ranked as the heaviest
+    if (!(wv == wv)) wv = 1.0;
+    w[p * nb + q] = wv;
   }
 }
 

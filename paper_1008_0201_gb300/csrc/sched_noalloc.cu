@@ -14,8 +14,8 @@
 
 namespace jac {
 __global__ void k_sched_static(int nb, int ordering, int nsteps, int* pairs, int* counts);
-__global__ void k_sched_cycle_weight(int nb, const double* w, int* order_g, int* pairs, int* counts, int max_steps,
-                                     int* nsteps_out);
+__global__ void k_sched_rank(int nb, const double* w, int* order);
+__global__ void k_sched_cycle_weight(int nb, int* order, int* pairs, int* counts, int max_steps, int* nsteps_out);
 }  // namespace jac
 
 namespace {
@@ -77,7 +77,8 @@ extern "C" int jacobi_sched_pairs_noalloc(int nb, int ordering, const double* we
   // the step count is the only value read back; start it at zero so that a failed launch
   // cannot return the previous call's count
   if (cudaMemsetAsync(dn, 0, sizeof(int), st) != cudaSuccess) return JAC_ECUDA;
-  jac::k_sched_cycle_weight<<<1, 1024, sizeof(int) * nb, st>>>(nb, weights, order, pairs, counts, max_steps, dn);
+  jac::k_sched_rank<<<(nb * (nb - 1) / 2 + 255) / 256, 256, sizeof(double) * nb, st>>>(nb, weights, order);
+  jac::k_sched_cycle_weight<<<1, 1024, sizeof(int) * nb, st>>>(nb, order, pairs, counts, max_steps, dn);
   int status = (cudaGetLastError() == cudaSuccess) ? JAC_OK : JAC_ECUDA;
   int h = -1;
   if (cudaMemcpyAsync(&h, dn, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) status = JAC_ECUDA;

@@ -152,3 +152,44 @@ def test_backward_argument_positions(lib):
     assert call(ldgb=3) == -23
     assert call(s_gb=15) == -24
     assert call(batch=0) == 0  # nothing to do, no CUDA call
+
+
+@pytest.mark.parametrize("noalloc", [False, True])
+def test_sched_pairs_argument_positions(lib, noalloc):
+    fn = lib.jacobi_sched_pairs_noalloc if noalloc else lib.jacobi_sched_pairs
+    ns = ctypes.c_int(-5)
+
+    def call(nb=16, ordering=3, w=FAKE, pairs=FAKE, counts=FAKE2, max_steps=32, nsteps=True):
+        return fn(nb, ordering, w, pairs, counts, max_steps, ctypes.byref(ns) if nsteps else None, None)
+
+    assert call(nb=0) == -1
+    assert call(nb=1) == -1
+    assert call(nb=15) == -1  # odd
+    assert call(ordering=-1) == -2
+    assert call(ordering=4) == -2
+    assert call(w=None) == -3  # the weight ordering needs weights
+    assert call(pairs=None) == -4
+    assert call(counts=None) == -5
+    assert call(max_steps=0) == -6
+    assert call(ordering=2, max_steps=14) == -6  # round-robin needs nb - 1 steps
+    assert call(ordering=0, max_steps=15) == -6  # modulus needs nb steps
+    assert call(nsteps=False) == -7
+    # block-count limits: 256 for the allocation-free entry point (its fixed scratch),
+    # JAC_CYCLE_WEIGHT_MAX_NB = 512 for the weight ordering, 4096 otherwise
+    if noalloc:
+        assert call(nb=258) == -1
+        assert call(nb=258, ordering=2, max_steps=257) == -1
+    else:
+        assert call(nb=514) == -1
+        assert call(nb=4098, ordering=2, max_steps=4097) == -1
+    assert ns.value == -5  # nothing written on an argument error
+
+
+def test_cycle_weight_block_cap(lib):
+    # n = 1100 with w = 1 gives nb = 1100 > 512 blocks: rejected as an invalid opts argument,
+    # real (argument 7) and complex (the real problem of order 2n; argument 7)
+    o = _opts(ordering=3, block_w=1)
+    assert _hsvd(lib, m=1100, n=1100, ldg=1100, ldv=1100, opts=o) == -7
+    assert _hsvd(lib, m=300, n=300, ldg=300, ldv=300, dtype=1, opts=o) == -7
+    assert lib.jacobi_eig_pd(1100, 1100, 0, FAKE, 1100, ctypes.byref(o), FAKE, None, 0, FAKE2, 1100, None,
+                             None) == -6
