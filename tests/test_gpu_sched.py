@@ -2,7 +2,10 @@
 
 The pair tables of one cycle (Sec. 2.4: modulus, modified modulus, round-robin; per-cycle
 largest-weight greedy ordering, a build extension) are integer index work, so the device
-tables must EQUAL the oracle's: same steps, same pairs in the same slots.  Weight matrices
+tables must EQUAL the oracle's: the same steps in the same order, each with the same pairs.
+The static orderings must also agree slot by slot (both list a step's pairs by increasing p);
+for the weight ordering the oracle lists a step's pairs in the order the greedy scan took them
+and the device by increasing p, so its steps are compared as sorted pair lists.  Weight matrices
 include many ties (few distinct values), where only the stated tie rule (enumeration order)
 makes the table unique.  Non-finite weights (NaN, +inf, -inf) are ranked by the documented
 total order (NaN last), which the oracle reproduces on the same weights with NaN replaced by
@@ -38,9 +41,16 @@ def _oracle_tables(nb, ordering, W=None):
     return oracle.pairs_cycle_weight(nb, W)
 
 
-def _assert_equal(got, ref, tag):
+def _by_p(t):
+    return t[np.lexsort((t[:, 1], t[:, 0]))] if len(t) else t
+
+
+def _assert_equal(got, ref, tag, sort_steps=False):
     assert len(got) == len(ref), (tag, len(got), len(ref))
     for s, (a, b) in enumerate(zip(got, ref)):
+        if sort_steps:
+            assert np.array_equal(a, _by_p(a)), (tag, s, "device step not listed by p")
+            b = _by_p(b)
         assert a.shape == b.shape and np.array_equal(a, b), (tag, s, a.tolist(), b.tolist())
 
 
@@ -75,7 +85,7 @@ def test_cycle_weight_equals_oracle(cuda_dev, nb, levels):
     ref = _oracle_tables(nb, "cycle_weight", W)
     for noalloc in (False, True):
         got = _dev_tables(nb, "cycle_weight", W, noalloc=noalloc)
-        _assert_equal(got, ref, ("cycle_weight", nb, levels, noalloc))
+        _assert_equal(got, ref, ("cycle_weight", nb, levels, noalloc), sort_steps=True)
     _assert_cover(ref, nb, "oracle")
 
 
@@ -84,7 +94,7 @@ def test_cycle_weight_all_equal_and_max_nb(cuda_dev):
     for nb in (32, 512):
         W = np.full((nb, nb), 0.25)
         got = _dev_tables(nb, "cycle_weight", W)
-        _assert_equal(got, _oracle_tables(nb, "cycle_weight", W), ("equal", nb))
+        _assert_equal(got, _oracle_tables(nb, "cycle_weight", W), ("equal", nb), sort_steps=True)
 
 
 @pytest.mark.parametrize("noalloc", [False, True])
@@ -98,4 +108,4 @@ def test_cycle_weight_non_finite(cuda_dev, noalloc):
     got = _dev_tables(nb, "cycle_weight", W, noalloc=noalloc)
     _assert_cover(got, nb, "non-finite")
     W2 = np.where(np.isnan(W), -np.inf, W)
-    _assert_equal(got, _oracle_tables(nb, "cycle_weight", W2), "non-finite vs oracle")
+    _assert_equal(got, _oracle_tables(nb, "cycle_weight", W2), "non-finite vs oracle", sort_steps=True)
