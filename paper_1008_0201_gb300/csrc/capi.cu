@@ -15,6 +15,8 @@
 #include <mutex>
 #include <vector>
 
+#include <cuda.h>
+
 #include "jacobi_common.cuh"
 #include "jacobi_gb300.h"
 
@@ -57,6 +59,11 @@ __global__ void k_restructure(int h, int n, const double* in, double* out, const
 __global__ void k_fill_uniform(double* x, long long n, unsigned long long seed);
 __global__ void k_gram_oz(const JacProb* probs, int s, int CS);
 __global__ void k_update_oz(const JacProb* probs, int s, int gslabs);
+__global__ void k_gram32_tc(const JacProb* probs, int s, int CS, const __grid_constant__ CUtensorMap tmG);
+__global__ void k_update32_tc(const JacProb* probs, int s, int gtiles, int tpc, const __grid_constant__ CUtensorMap tmG,
+                              const __grid_constant__ CUtensorMap tmV);
+size_t tc_gram32_smem_bytes();
+size_t tc_update32_smem_bytes();
 size_t oz_gram_smem_bytes();
 size_t oz_update_smem_bytes();
 int oz_gemm_launch(int Mr, int Nc, int K, const double* A, int lda, int transA, const double* B, int ldb,
@@ -156,6 +163,11 @@ int setup_attributes(int dev) {
   ok &= cudaFuncSetAttribute(k_gram_oz, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess;
   ok &= cudaFuncSetAttribute(k_update_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_update_smem_bytes()) ==
         cudaSuccess;
+  ok &= cudaFuncSetAttribute(k_gram32_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_gram32_smem_bytes()) ==
+        cudaSuccess;
+  ok &= cudaFuncSetAttribute(k_gram32_tc, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess;
+  ok &= cudaFuncSetAttribute(k_update32_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)tc_update32_smem_bytes()) == cudaSuccess;
   ok &= pivot_set_attributes() == 0;
   ok &= pivot64_set_attributes() == 0;
   ok &= cudaFuncSetAttribute(k_rank, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024) == cudaSuccess;
@@ -180,6 +192,49 @@ struct Arena {
     return p;
   }
 };
+
+// TMA tensor maps of the FP32 copies of one problem (FP32 sweeps on the tensor cores): 2-D
+// column-major (rows contiguous), 32 x 32 boxes, 128-byte swizzle.  cuTensorMapEncodeTiled comes
+// from the driver through the runtime's entry-point query (no link against the driver library).
+struct TcMaps {
+  CUtensorMap g32, v32;
+};
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+std::mutex g_encode_mutex;
+EncodeTiledFn g_encode = nullptr;
+
+EncodeTiledFn encode_fn() {
+  std::lock_guard<std::mutex> lk(g_encode_mutex);
+  if (!g_encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    g_encode = reinterpret_cast<EncodeTiledFn>(fn);
+  }
+  return g_encode;
+}
+
+// rows x cols FP32, leading dimension ld (rows <= ld, ld * 4 a multiple of 16, base 16-byte aligned)
+int encode_f32_map(CUtensorMap* m, float* base, int rows, int cols, int ld) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc || !base || (ld * 4) % 16 || (reinterpret_cast<uintptr_t>(base) & 15)) return JAC_ECUDA;
+  cuuint64_t dims[2] = {(cuuint64_t)rows, (cuuint64_t)cols};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
+  cuuint32_t box[2] = {32, 32};
+  cuuint32_t es[2] = {1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+                 CUDA_SUCCESS
+             ? 0
+             : JAC_ECUDA;
+}
 
 int check_opts(const jac_opts& o, int argpos, bool batch) {
   if (o.block_w < 1 || o.block_w > JAC_WMAX) return -argpos;
@@ -316,12 +371,20 @@ void carve_problem(Arena& ar, const Plan& P, JacProb& d, JacIO& io, bool weights
 // One launch of the three step kernels for every problem of a class array.
 // fallback = false leaves out the FP64 pivot kernel: blocks the FP32 pivot hands over are then
 // not rotated in this step (the FP32 sweeps of the mixed mode switch to FP64 on a handover).
+// Work split of the tensor-core FP32 update: 128-row tiles of G32 then V32, ysplit CTAs per pair.
+struct TcSplit {
+  int gtiles = 0, ysplit = 1, tpc = 1;
+};
+
 int launch_step(JacProb* dprobs, int count, int km, int max_half, int gslabs, int tslabs, int CS, int CS32, int s,
                 bool lowp, bool fallback, const PivotParams& pp, cudaStream_t st, ProfRun& prof,
-                long long& launches) {
+                long long& launches, const TcMaps* maps = nullptr, const TcSplit* tsp = nullptr) {
   int r = 0;
   size_t pm = prof.pre(JAC_KERNEL_GRAM, st);
-  if (lowp)
+  if (lowp && maps)
+    r = launch_cluster(k_gram32_tc, dim3(max_half * CS32, count), CS32, 128, tc_gram32_smem_bytes(), st,
+                       (const JacProb*)dprobs, s, CS32, maps->g32);
+  else if (lowp)
     r = launch_cluster(k_gram32, dim3(max_half * CS32, count), CS32, 128, 0, st, (const JacProb*)dprobs, s, CS32);
   else if (pp.oz)
     r = launch_cluster(k_gram_oz, dim3(max_half * CS, count), CS, 256, oz_gram_smem_bytes(), st,
@@ -335,7 +398,10 @@ int launch_step(JacProb* dprobs, int count, int km, int max_half, int gslabs, in
   if (fallback) pivot64_launch(km, max_half, count, st, dprobs, s, pp);  // blocks the FP32 kernel handed over
   prof.post(pm, st);
   pm = prof.pre(JAC_KERNEL_UPDATE, st);
-  if (lowp)
+  if (lowp && maps && tsp)
+    k_update32_tc<<<dim3(max_half, tsp->ysplit, count), 128, tc_update32_smem_bytes(), st>>>(
+        dprobs, s, tsp->gtiles, tsp->tpc, maps->g32, maps->v32);
+  else if (lowp)
     k_update32<<<dim3(max_half, tslabs, count), 256, 0, st>>>(dprobs, s, gslabs);
   else if (pp.oz)
     k_update_oz<<<dim3(max_half, tslabs, count), 256, oz_update_smem_bytes(), st>>>(dprobs, s, gslabs);
@@ -518,6 +584,21 @@ int solve_real(int m, int n, int dtype, void* Gv, int ldg, const int8_t* Jdev, c
   ck(cudaMemcpyAsync(L.jsoff, &zero, sizeof(long long), cudaMemcpyHostToDevice, st));
   ck(cudaMemsetAsync(L.flags, 0, sizeof(unsigned), st));
 
+  // FP32 sweeps of a single solve run on the tensor cores (TMA tensor maps of the FP32 copies)
+  TcMaps tmaps;
+  TcSplit tsplit;
+  bool use_tc = false;
+  if (lowp && status == JAC_OK) {
+    use_tc = encode_f32_map(&tmaps.g32, hp.G32, P.mp, n, P.mp) == 0;
+    if (use_tc) use_tc = encode_f32_map(&tmaps.v32, hp.V32 ? hp.V32 : hp.G32, hp.V32 ? P.np : P.mp, n,
+                                        hp.V32 ? P.np : P.mp) == 0;
+    tsplit.gtiles = (P.mp + 127) / 128;
+    const int ntiles = tsplit.gtiles + (hp.V32 ? (P.np + 127) / 128 : 0);
+    tsplit.ysplit = std::max(1, std::min(ntiles, (2 * 152 + P.half - 1) / P.half));
+    tsplit.tpc = (ntiles + tsplit.ysplit - 1) / tsplit.ysplit;
+    tsplit.ysplit = (ntiles + tsplit.tpc - 1) / tsplit.tpc;
+  }
+
   long long launches = 0;
   k_sort_signs<<<1, 32, 0, st>>>(L.probs, L.io, L.Js, L.jsoff);
   k_check_finite<<<dim3(std::min(1024, (int)(((size_t)m * n + 255) / 256)), 1), 256, 0, st>>>(L.probs, L.io);
@@ -612,7 +693,7 @@ int solve_real(int m, int n, int dtype, void* Gv, int ldg, const int8_t* Jdev, c
     auto record = [&](cudaStream_t ss, long long& nl, ProfRun& pr) -> int {
       for (int s = 0; s < nsteps; ++s)
         if (int r = launch_step(L.probs, 1, P.km, P.half, gslabs, tslabs, CS, CS32, s, low, phase != 1, pp, ss, pr,
-                                nl))
+                                nl, use_tc ? &tmaps : nullptr, use_tc ? &tsplit : nullptr))
           return r;
       k_sweep_reduce<<<1, 256, 0, ss>>>(L.probs, L.io, L.rec, 0, nullptr);
       ++nl;
@@ -650,6 +731,10 @@ int solve_real(int m, int n, int dtype, void* Gv, int ldg, const int8_t* Jdev, c
     // a block the FP32 pivot could not factor or J-orthogonalize was handed over (and, in the
     // FP32 sweeps, left unrotated): the FP64 phase decides it
     bool lowp_singular = phase == 1 && (hrec.err & JAC_DEVERR_HANDOVER);
+    if (hrec.err & JAC_DEVERR_TIMEOUT) {  // a bounded wait in a tensor-core kernel gave up
+      status = JAC_EINTERNAL;
+      break;
+    }
     if (hrec.err & JAC_DEVERR_NOTPD) {
       if (phase != 1) {
         status = JAC_ENOTPD;
@@ -1176,6 +1261,7 @@ int solve_batched(int batch, const int* m, const int* n, int dtype, void* const*
     int s = JAC_OK;
     if (hio_back[i].flags & 2) s = -7;
     else if (hio_back[i].flags & 1) s = JAC_ENONFINITE;
+    else if (flags_back[i] & JAC_DEVERR_TIMEOUT) s = JAC_EINTERNAL;
     else if (flags_back[i] & JAC_DEVERR_NOTPD) s = JAC_ENOTPD;
     else if (hp_back[i].active) s = JAC_ENOTCONV;
     if (status != JAC_OK) s = status;

@@ -21,6 +21,7 @@
 #define JAC_DEVERR_INNER_LIMIT 2u
 #define JAC_DEVERR_NONFINITE 4u
 #define JAC_DEVERR_HANDOVER 8u  // a pivot block went to the FP64 pivot kernel (not an error)
+#define JAC_DEVERR_TIMEOUT 16u  // a bounded wait on a TMA load or tensor-core MMA gave up
 
 namespace jac {
 
