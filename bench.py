@@ -1,18 +1,25 @@
-"""Benchmark: time to solution of the hyperbolic one-sided block Jacobi method on one GB300.
+"""Benchmark: time to solution of the one-sided block Jacobi method on one GB300.
 
-Workload (one "step" = one full solve through the C ABI): G 512 x 512 Gaussian, J = diag(+1 x 256,
--1 x 256), block width 32, J_P-sign-pivoted Cholesky (Algorithm 3.3) and the per-cycle
-largest-off-weight ordering, tol = n 2^-53, V accumulated.  Reported metric: matrices/s
-(= 1000 / ms per solve), with the result checked against the tolerances of the test suite.
+Headline workload (one "step" = one full solve through the C ABI): the graded positive definite
+complex Hermitian problem of order n = 4096, G = B D with B complex Gaussian (re, im i.i.d.
+N(0, 1/2)) and D = diag(10^(-8 i / n)), J = I, V accumulated; block width 32 real columns,
+block-oriented sweeps (HB, Sec. 2.2), round-robin ordering, FP32 sweeps on the tensor cores then
+FP64 polish sweeps (mixed precision).  It is the largest configuration of the benchmark set that
+runs on one GPU.  Metric: matrices/s (= 1000 / ms per solve); the eigenvalues are checked against
+the oracle's stored result for the same seeded input.  The other configurations (the 64 x 64 PD
+case, the 512 x 512 hyperbolic case in mixed and FP64 forms, the 10 000-problem batch, the
+differentiation batch) are reported under other_workloads.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
 
 N > 1 runs independent replicas (one matrix per rank per step; the method has no exchange on
-one GPU), launched by torch.distributed.run.  --impl reference times the CPU oracle on the
-host cores on the same workload.
+one GPU), launched by torch.distributed.run.  --impl reference times the CPU oracle on the host
+cores on a bounded sample of the same workload, scaled to the full order.
 """
 import argparse
+import hashlib
 import json
+import multiprocessing as mp
 import os
 import statistics
 import subprocess
@@ -25,39 +32,38 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-N = 512
+N3 = 4096
 BLOCK_W = 32
 EPS = 2.0 ** -53
 METRIC = "time-to-solution and matrices/s at stated eigen rel-error; % FP64/FP32 tensor peak"
-WORKLOAD = "hyperbolic SVD 512x512 Gaussian, J=diag(+1x256,-1x256), w=32"
-
-
-def variant_name(args):
-    """Paper's naming (Sec. 3.2): H + F (full block) / B (block-oriented) + SC (sign-pivoted
-    Cholesky), with the block ordering."""
-    name = "H" + ("B" if args.block_mode == "oriented" else "F") + ("SC" if args.factor == "chol_signpiv" else "")
-    return "%s, %s ordering" % (name, args.ordering.replace("_", "-"))
-# dtype of the arithmetic: FP64 contractions and FP32 inner rotations; the mixed mode runs its
-# early sweeps on an FP32 copy (FP32 products) before the FP64 polish
+WORKLOAD = ("graded complex Hermitian PD n=4096: G = B D, B complex Gaussian, D = diag(10^(-8i/n)), J = I; "
+            "w = 32 real (16 complex) columns, block-oriented (HB), round-robin, FP32 tensor-core sweeps + "
+            "FP64 polish, V accumulated")
+SAMPLE_N = 768  # order of the oracle's bounded sample of the headline workload
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of kernels captured with
+# ncu on the headline workload's kernels, per unit of work; None until captured for the kernel
+# as it is now (profiles/ holds the capture summaries)
+TRAFFIC_PER_PAIR = {}
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-other-workloads", action="store_true")
+    ap.add_argument("--workload", default="c3", choices=["c3", "c2", "paper_e1"],
+                    help="c2: the 512 x 512 hyperbolic case as the timed workload; paper_e1: the "
+                         "paper-shaped run (symmetric uniform [-5,5] H of order --n, Bunch-Parlett "
+                         "factored on the host, hyperbolic solve); neither is the headline")
+    ap.add_argument("--n", type=int, default=2000)
+    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp32_only"])
+    ap.add_argument("--f64-products", default="split16", choices=["mma", "split16"])
     ap.add_argument("--ordering", default="round_robin")
     ap.add_argument("--factor", default="chol_signpiv")
     ap.add_argument("--block-mode", default="oriented", choices=["full", "oriented"])
-    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp32_only"])
-    ap.add_argument("--f64-products", default="split16", choices=["mma", "split16"])
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-other-workloads", action="store_true")
-    ap.add_argument("--workload", default="c2", choices=["c2", "paper_e1"],
-                    help="paper_e1: the paper-shaped run (symmetric uniform [-5,5] H of order --n, "
-                         "Bunch-Parlett factored on the host, hyperbolic solve); not the headline")
-    ap.add_argument("--n", type=int, default=2000)
     return ap.parse_args()
 
 
@@ -67,6 +73,13 @@ def load_peaks():
         with open(p) as f:
             return json.load(f), "measured"
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def variant_name(args):
+    """Paper's naming (Sec. 3.2): H + F (full block) / B (block-oriented) + SC (sign-pivoted
+    Cholesky), with the block ordering."""
+    name = "H" + ("B" if args.block_mode == "oriented" else "F") + ("SC" if args.factor == "chol_signpiv" else "")
+    return "%s, %s ordering" % (name, args.ordering.replace("_", "-"))
 
 
 class ClockSampler:
@@ -121,87 +134,195 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(steps_budget_s=20.0):
-    """The oracle as it stands, 1 host core, full solves of the same workload until ~budget."""
+def read_golden(n):
+    """The oracle's stored eigenvalues of the graded complex workload of order n (written by
+    tests/golden/make_c3_golden.py), or None."""
+    path = os.path.join(ROOT, "tests", "golden", "c3_graded_complex_n%d.txt" % n)
+    if not os.path.exists(path):
+        return None
+    meta, lam, in_lam = {}, [], False
+    with open(path) as f:
+        for ln in f:
+            ln = ln.strip()
+            if not ln or ln.startswith("#"):
+                continue
+            if ln == "lambda":
+                in_lam = True
+                continue
+            if in_lam:
+                lam.append(float(ln))
+            else:
+                k, v = ln.split(None, 1)
+                meta[k] = v
+    meta["lambda"] = np.array(lam)
+    return meta
+
+
+def draws_hash(n):
+    """sha256 of the Gaussian draws of the graded complex workload (same as the golden writer)."""
+    from paper_1008_0201_gb300 import inputs
+
+    g = inputs.rng(3, 0)
+    h = hashlib.sha256()
+    h.update(np.ascontiguousarray(g.standard_normal((n, n))).tobytes())
+    h.update(np.ascontiguousarray(g.standard_normal((n, n))).tobytes())
+    return h.hexdigest()
+
+
+# ------------------------------------------------------------------ CPU baselines (the oracle)
+def oracle_c3_sample(n=SAMPLE_N):
+    """One oracle solve of the graded complex workload of order n (same generator): seconds, sweeps."""
     import oracle
     from paper_1008_0201_gb300 import inputs
 
-    G, J = inputs.config2_hyperbolic(n=N)
-    oracle.solve(G[:64, :64], J[:64])  # build + warm
-    times = []
-    t_all = time.perf_counter()
-    while True:
+    G, J = inputs.config3_graded_complex(n)
+    t0 = time.perf_counter()
+    r = oracle.solve(G, J, want_v=True)
+    return time.perf_counter() - t0, r["sweeps"]
+
+
+def c3_scale(t_sample, sweeps_sample):
+    """Oracle seconds for the full order: the sample's time per sweep x (4096 / n)^3 (one sweep is
+    n^2/2 pairs of 4n-term complex columns) x the oracle's own sweep count at n = 4096 (stored
+    with its eigenvalues), else the sample's."""
+    g = read_golden(N3)
+    sweeps_full = int(g["oracle_sweeps"]) if g else sweeps_sample
+    return t_sample / sweeps_sample * (N3 / SAMPLE_N) ** 3 * sweeps_full, sweeps_full, g is not None
+
+
+def cpu_baseline():
+    import oracle
+
+    oracle.load()
+    t, sw = oracle_c3_sample()
+    full_s, sweeps_full, from_golden = c3_scale(t, sw)
+    return {"value": 1.0 / full_s, "unit": "matrices/s", "cores": 1, "kind": "oracle",
+            "sample": "one oracle solve of the same graded complex workload at order %d (%d sweeps, %.1f s, "
+                      "1 core), scaled to order %d by time per sweep x (%d/%d)^3 x %d sweeps (%s)"
+                      % (SAMPLE_N, sw, t, N3, N3, SAMPLE_N, sweeps_full,
+                         "the oracle's own count at n=4096" if from_golden else "the sample's count")}
+
+
+def _oracle_solve_one(args):
+    import oracle
+
+    G, J = args
+    t0 = time.perf_counter()
+    oracle.solve(G, J, want_v=True)
+    return time.perf_counter() - t0
+
+
+def oracle_pool_rate(problems, label):
+    """The oracle over a list of (G, J) problems on every host core (spawned processes)."""
+    cores = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        pool.map(_oracle_solve_one, problems[: cores])  # start-up and oracle build
         t0 = time.perf_counter()
-        r = oracle.solve(G, J)
-        times.append(time.perf_counter() - t0)
-        if time.perf_counter() - t_all > steps_budget_s or len(times) >= 5:
-            break
-    mean = sum(times) / len(times)
-    return {"value": 1.0 / mean, "unit": "matrices/s", "cores": 1, "kind": "oracle",
-            "sample": "%d full solves of the 512x512 hyperbolic problem (row-cyclic pointwise one-sided "
-                      "Jacobi, %d sweeps), %.2f s each" % (len(times), r["sweeps"], mean)}
+        per = pool.map(_oracle_solve_one, problems, chunksize=max(1, len(problems) // (8 * cores)))
+        wall = time.perf_counter() - t0
+    return {"value": len(problems) / wall, "unit": "matrices/s", "cores": cores, "kind": "oracle",
+            "one_core_matrices_per_s": len(problems) / sum(per),
+            "sample": "%s: %d problems, oracle on %d processes (spawned), %.1f s wall" % (label, len(problems),
+                                                                                      cores, wall)}
+
+
+def cpu_baselines_batches():
+    from paper_1008_0201_gb300 import inputs
+
+    out = {}
+    Gs, Js = inputs.config4_batched()
+    out["c4"] = oracle_pool_rate(list(zip(Gs, Js)), "all 10000 batched problems, orders 8..128")
+    Gc, _, _ = inputs.config5_backward()
+    H = np.einsum("bij,bkj->bik", Gc, Gc) + 0.1 * np.eye(Gc.shape[1])
+    L = np.linalg.cholesky(H)
+    ones = np.ones(Gc.shape[1], dtype=np.int8)
+    out["c5_forward"] = oracle_pool_rate([(L[b], ones) for b in range(L.shape[0])],
+                                         "all 256 differentiation problems of order 256 (Cholesky factors)")
+    return out
 
 
 def reference_arm(args, rank, world):
+    """The oracle as it stands on the host cores: each step one oracle solve of the order-768 sample
+    of the headline workload, reported as matrices/s of the full order (scaled as cpu_baseline)."""
     if rank != 0:
         return 0
     import oracle
     from paper_1008_0201_gb300 import inputs
 
-    G, J = inputs.config2_hyperbolic(n=N)
+    oracle.load()
     for _ in range(args.warmup):
-        oracle.solve(G[:128, :128], J[:128])  # bounded warm-up sample
-    t0 = time.perf_counter()
-    sweeps = 0
+        G, J = inputs.config3_graded_complex(128)
+        oracle.solve(G, J)  # bounded warm-up sample
+    ts, sw = [], 0
     for _ in range(args.steps):
-        r = oracle.solve(G, J)
-        sweeps = r["sweeps"]
-    dt = (time.perf_counter() - t0) / args.steps
-    val = 1.0 / dt
+        t, sw = oracle_c3_sample()
+        ts.append(t)
+    full_s, sweeps_full, from_golden = c3_scale(float(np.mean(ts)), sw)
+    val = 1.0 / full_s
+    sample = ("each step one oracle solve of the graded complex workload at order %d (%d sweeps, %.1f s mean), "
+              "scaled to order %d by time per sweep x (%d/%d)^3 x %d sweeps (%s); warm-up on order 128"
+              % (SAMPLE_N, sw, float(np.mean(ts)), N3, N3, SAMPLE_N, sweeps_full,
+                 "the oracle's own count at n=4096" if from_golden else "the sample's count"))
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "matrices/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": full_s * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD + ", row-cyclic pointwise oracle", "n": N},
-            "cpu_baseline": {"value": val, "unit": "matrices/s", "cores": 1, "kind": "oracle",
-                             "sample": "each step one full solve (%d sweeps); warm-up on 128x128" % sweeps},
+            "config": {"workload": WORKLOAD + "; row-cyclic pointwise oracle", "n": N3},
+            "cpu_baseline": {"value": val, "unit": "matrices/s", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": val, "unit": "matrices/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
 
 
+# ------------------------------------------------------------------ secondary workloads
+def timed_ms(fn, reps, stream):
+    """Mean ms of reps calls of fn, CUDA events on the current stream, after one warm-up call."""
+    import torch
+
+    fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
 def other_workloads(dev, steps=3):
-    """Secondary measurements of the other configurations (rank 0, after the headline).  Each is
-    the mean of `steps` solves timed with CUDA events on the current stream, inputs in HBM."""
+    """The other configurations (rank 0, after the headline), inputs in HBM, CUDA-event timed."""
     import torch
 
     from paper_1008_0201_gb300 import binding, inputs
 
     stream = torch.cuda.current_stream(dev)
     out = {}
-
-    def timed(fn, reps):
-        fn()  # warm-up
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(reps):
-            fn()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / reps
-
-    # C2 in plain FP64 (HFSC, per-cycle weight): the form the mixed-precision headline is compared to
+    # C2: 512 x 512 hyperbolic, w = 32; HBSC round-robin in mixed and plain FP64 (like for like),
+    # and HFSC with the per-cycle weight ordering in FP64
     G, J = inputs.config2_hyperbolic()
     Gd = torch.from_numpy(G).to(dev)
     Jd = torch.from_numpy(J).to(dev)
-    o64 = binding.default_opts(block_w=32, ordering="cycle_weight", block_mode="full", precision="fp64")
-    out["c2_hfsc_fp64_ms"] = timed(lambda: binding.jacobi_hsvd(Gd, Jd, o64), steps)
-    # C1: 64 x 64 positive definite, w = 8, modulus ordering
+    c2 = {}
+    for name, kw in (("hbsc_rr_mixed", dict(block_mode="oriented", ordering="round_robin", precision="fp32")),
+                     ("hbsc_rr_fp64", dict(block_mode="oriented", ordering="round_robin", precision="fp64")),
+                     ("hfsc_cycle_weight_fp64", dict(block_mode="full", ordering="cycle_weight", precision="fp64"))):
+        o = binding.default_opts(block_w=32, factor="chol_signpiv", **kw)
+        res = {}
+
+        def run(o=o, res=res):
+            res["o"] = binding.jacobi_hsvd(Gd, Jd, o)
+        ms = timed_ms(run, steps * 3, stream)
+        info = res["o"]["info"]
+        c2[name] = {"ms": ms, "matrices_per_s": 1e3 / ms, "sweeps": info["sweeps"],
+                    "fp32_sweeps": info["lowp_sweeps"]}
+    out["c2_hyperbolic_512"] = c2
+    # C1: 64 x 64 positive definite, w = 8, modulus ordering, FP64
     G1, _ = inputs.config1_pd()
     G1d = torch.from_numpy(G1).to(dev)
     o1 = binding.default_opts(block_w=8, ordering="modulus", block_mode="full", precision="fp64")
-    out["c1_pd64_fp64_ms"] = timed(lambda: binding.jacobi_eig_pd(G1d, o1), steps)
+    out["c1_pd64_fp64_ms"] = timed_ms(lambda: binding.jacobi_eig_pd(G1d, o1), steps, stream)
     # C4: 10 000 problems of order 8..128, FP64 and FP32-only, against one call per problem
     Gs, Js = inputs.config4_batched()
     ns = np.array([x.shape[1] for x in Gs], dtype=np.int32)
@@ -213,25 +334,35 @@ def other_workloads(dev, steps=3):
     lam = torch.empty(int(joffs[-1]), dtype=torch.float64, device=dev)
     Vb = torch.empty(int(offs[-1]), dtype=torch.float64, device=dev)
     ptr = lambda t, o, es: (np.uint64(t.data_ptr()) + o[:-1].astype(np.uint64) * np.uint64(es)).astype(np.uint64)
+    last = {}
 
     def batched(prec):
         ob = binding.default_opts(precision=prec, want_v=1)
 
         def run():
             Gw.copy_(G0)
-            binding.jacobi_eig_batched_raw(ns, ns, ptr(Gw, offs, 8), ns, ptr(Jb, joffs, 1), ob, ptr(lam, joffs, 8),
-                                           None, None, ptr(Vb, offs, 8), ns, stream.cuda_stream, want_info=False)
+            last[prec] = binding.jacobi_eig_batched_raw(ns, ns, ptr(Gw, offs, 8), ns, ptr(Jb, joffs, 1), ob,
+                                                        ptr(lam, joffs, 8), None, None, ptr(Vb, offs, 8), ns,
+                                                        stream.cuda_stream, want_info=True)
         return run
 
-    ms64_default = timed(batched("fp64"), 2)
-    # the library's width autotuner, per precision (about a second each)
+    ms64_default = timed_ms(batched("fp64"), 2, stream)
     rules64 = binding.jacobi_autotune_batched(count=256, precision="fp64", device=dev)
-    ms64 = timed(batched("fp64"), 2)
+    ms64 = timed_ms(batched("fp64"), 2, stream)
     rules32 = binding.jacobi_autotune_batched(count=256, precision="fp32_only", device=dev)
-    ms32 = timed(batched("fp32_only"), 2)
+    ms32 = timed_ms(batched("fp32_only"), 2, stream)
     binding.jacobi_autotune_batched(count=0, device=dev)
     show = lambda r: {"%d-%d" % (lo, hi): int(r[lo]) for lo, hi in ((8, 16), (17, 32), (33, 48), (49, 64),
                                                                       (65, 96), (97, 128))}
+
+    def statuses(prec):
+        st = last.get(prec)
+        infos = st[1] if isinstance(st, tuple) and len(st) > 1 else None
+        if not infos:
+            return None
+        codes = [int(i.status) for i in infos]
+        return {"ok": sum(c == 0 for c in codes), "not_pd_in_this_precision": sum(c == 2 for c in codes),
+                "other": sum(c not in (0, 2) for c in codes)}
     sample = 200
     oloop = binding.default_opts(block_w=16, ordering="round_robin", precision="fp64")
     Gl = [torch.from_numpy(x).to(dev) for x in Gs[:sample]]
@@ -240,10 +371,11 @@ def other_workloads(dev, steps=3):
     def loop():
         for a, b in zip(Gl, Jl):
             binding.jacobi_hsvd(a, b, oloop, raise_on_error=False)
-    msl = timed(loop, 1)
+    msl = timed_ms(loop, 1, stream)
     out["c4_batched_fp64"] = {"ms": ms64, "matrices_per_s": len(Gs) * 1e3 / ms64, "width_rules": show(rules64),
-                              "untuned_ms": ms64_default}
-    out["c4_batched_fp32_only"] = {"ms": ms32, "matrices_per_s": len(Gs) * 1e3 / ms32, "width_rules": show(rules32)}
+                              "untuned_ms": ms64_default, "problem_status": statuses("fp64")}
+    out["c4_batched_fp32_only"] = {"ms": ms32, "matrices_per_s": len(Gs) * 1e3 / ms32, "width_rules": show(rules32),
+                                   "problem_status": statuses("fp32_only")}
     out["c4_one_call_per_problem_fp64"] = {"sample": sample, "matrices_per_s": sample * 1e3 / msl}
     # C5: forward (batched, 256 problems of order 256) and the backward kernel
     Gc, w, C = inputs.config5_backward()
@@ -254,45 +386,65 @@ def other_workloads(dev, steps=3):
 
     def fwd():
         res["o"] = binding.jacobi_eig_batched_uniform(L, None, o5)
-    ms_f = timed(fwd, 2)
+    ms_f = timed_ms(fwd, 2, stream)
     lamr, Ur = res["o"]["lam"], res["o"]["U"]
     wt = torch.from_numpy(w).to(dev).expand_as(lamr).contiguous()
     Ct = torch.from_numpy(C).to(dev)
     Ub = torch.zeros_like(Ur)
     Ub[..., :8] = 2.0 * Ct @ (Ct.T @ Ur[..., :8])
-    ms_b = timed(lambda: binding.jacobi_eig_backward(lamr, Ur, wt, Ub), 3)
+    ms_b = timed_ms(lambda: binding.jacobi_eig_backward(lamr, Ur, wt, Ub), 3, stream)
     n5 = Gc.shape[1]
     out["c5_forward"] = {"ms": ms_f, "matrices_per_s": Gc.shape[0] * 1e3 / ms_f}
     out["c5_backward"] = {"ms": ms_b, "tflops_fp64": 3 * 2 * Gc.shape[0] * n5 ** 3 / (ms_b * 1e-3) / 1e12}
-    # C3 at reduced order (the full n = 4096 takes ~30 s): graded complex, mixed precision
-    G3, _ = inputs.config3_graded_complex(n=1024)
-    G3d = torch.from_numpy(G3).to(dev)
-    o3 = binding.default_opts(block_w=32, ordering="round_robin", block_mode="oriented", precision="fp32")
-    out["c3_graded_complex_n1024_ms"] = timed(lambda: binding.jacobi_eig_pd(G3d, o3), 1)
     return out
 
 
-def max_over_ranks(value, dist, device):
-    """The largest of each rank's value (replicas: the slowest rank sets the whole job's time)."""
-    if dist is None:
-        return value
-    import torch
-
-    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
-
-
-def job_value(world, ms):
-    """Whole-job matrices/s: every rank solved one matrix in at most `ms` milliseconds."""
-    return world * 1000.0 / ms
-
-
-def replica_input(rank):
-    """Rank r solves its own seeded draw of the 512 hyperbolic workload (no data exchange)."""
-    from paper_1008_0201_gb300 import inputs
-
-    return inputs.config2_hyperbolic(n=N, salt=rank)
+# ------------------------------------------------------------------ kernel evidence
+def kernel_evidence(prof, info, m, n, half, k, peaks):
+    """Per-kernel achieved rate against its roofline, from one solve with every step kernel
+    bracketed by CUDA events on the solve's stream (jacobi_profile_*).  Algorithmic work per
+    launch (units: pivot pairs of a step; all pairs take the Gram and the pivot, only rotated
+    pairs the update):
+      FP32-sweep Gram (tcgen05 kind::tf32, 3 products h h', h l', l h'):  3 * 2 m k^2 per pair
+      FP32-sweep update (same):                                         3 * 2 (m + n) k^2 per rotated pair
+      FP64 Gram (FP16 digit products, 36 per multiply-add):             36 * m k (k + 1) per pair
+      FP64 update (43 digit products per multiply-add):                 43 * 2 (m + n) k^2 per rotated pair
+      pivot (HBM, A_P read + V_P written, k x k FP64 each):             2 * 8 k^2 bytes per pair
+    The tf32 peak is the measured bf16 peak x 1.1 / 2.25 (nominal tf32 / bf16 dense rates);
+    the FP16 peak equals the bf16 one."""
+    bf16 = peaks["bf16_tflops"]
+    tf32 = bf16 * 1.1 / 2.25
+    hbm = peaks["hbm_gbs"]
+    rot_lowp = info["pivots_rotated_lowp"]
+    rot64 = info["pivots_rotated"] - rot_lowp
+    ev = {}
+    total = sum(v[0] for v in prof.values()) or 1e-30
+    for name, (ms, launches) in prof.items():
+        if launches == 0:
+            continue
+        avg_s = ms / launches * 1e-3
+        e = {"launches": launches, "total_ms": ms, "avg_us": avg_s * 1e6, "share": ms / total}
+        if name == "gram_lowp":
+            fl = half * 3 * 2 * m * k * k
+            e.update(bound="tensor", dtype="tf32x3", achieved=fl / avg_s / 1e12, peak=tf32, unit="TFLOP/s")
+        elif name == "update_lowp":
+            fl = rot_lowp / launches * 3 * 2 * (m + n) * k * k
+            e.update(bound="tensor", dtype="tf32x3", achieved=fl / avg_s / 1e12, peak=tf32, unit="TFLOP/s")
+        elif name == "gram":
+            fl = half * 36 * m * k * (k + 1)
+            e.update(bound="tensor", dtype="f16 digits", achieved=fl / avg_s / 1e12, peak=bf16, unit="TFLOP/s",
+                     fp64_equivalent_tflops=half * m * k * (k + 1) / avg_s / 1e12)
+        elif name == "update":
+            fl = rot64 / launches * 43 * 2 * (m + n) * k * k
+            e.update(bound="tensor", dtype="f16 digits", achieved=fl / avg_s / 1e12, peak=bf16, unit="TFLOP/s",
+                     fp64_equivalent_tflops=fl / 43 / avg_s / 1e12)
+        elif name == "pivot":
+            by = half * 2 * 8 * k * k
+            e.update(bound="hbm", achieved=by / avg_s / 1e9, peak=hbm, unit="GB/s",
+                     note="latency-bound on one SM per pair (dependent 2x2 rotations); HBM figure as asked")
+        e["frac"] = e["achieved"] / e["peak"]
+        ev[name] = e
+    return ev
 
 
 def paper_e1(args):
@@ -339,6 +491,64 @@ def paper_e1(args):
     return 0
 
 
+def max_over_ranks(value, dist, device):
+    """The largest of each rank's value (replicas: the slowest rank sets the whole job's time)."""
+    if dist is None:
+        return value
+    import torch
+
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, ms):
+    """Whole-job matrices/s: every rank solved one matrix in at most `ms` milliseconds."""
+    return world * 1000.0 / ms
+
+
+def replica_input(rank, workload="c3", n=N3):
+    """Rank r solves its own seeded draw (salt r) of the workload: replicas exchange no data."""
+    from paper_1008_0201_gb300 import inputs
+
+    if workload == "c2":
+        return inputs.config2_hyperbolic(salt=rank)
+    return inputs.config3_graded_complex(n, salt=rank)
+
+
+def headline_input(args, rank):
+    G, J = replica_input(rank, args.workload)
+    return G, J, args.workload != "c2"
+
+
+def accuracy(G, J, cplx, lam, Vn, info, rank):
+    """Eigenvalues against the oracle: the stored result of the full-size graded complex workload
+    (same draws, checked by hash), or a fresh oracle solve of the 512 hyperbolic case."""
+    import oracle
+
+    n = G.shape[1]
+    Bh = G / np.linalg.norm(G, axis=0)
+    if cplx:
+        g = read_golden(n)
+        if g is None or rank != 0 or g.get("draws_sha256") != draws_hash(n):
+            return {"checked": False, "reason": "no stored oracle result for this input"}
+        kb = float(g["kappa2_bhat"])
+        ref = g["lambda"]
+        rel = float(np.max(np.abs(lam - ref) / np.abs(ref)))
+        return {"checked": True, "against": "stored oracle eigenvalues (tests/golden)", "eig_rel_err": rel,
+                "eig_bound": 50 * n * EPS * kb * kb, "eig_bound_kappa_bhat": 50 * n * EPS * kb,
+                "ok": bool(rel <= 50 * n * EPS * kb * kb), "ok_kappa_bhat": bool(rel <= 50 * n * EPS * kb),
+                "max_scaled_off": info["max_scaled_off"], "tol": n * EPS}
+    ref = oracle.solve(G, J)
+    kap = np.linalg.cond(Bh) ** 2
+    rel = float(np.max(np.abs(lam - ref["lam"]) / np.abs(ref["lam"])))
+    J_out = np.where(lam < 0, -1, 1).astype(np.int8)
+    vjv = oracle.check_vjv(Vn, J, J_out)
+    return {"checked": True, "against": "oracle solve", "eig_rel_err": rel, "eig_bound": 50 * n * EPS * kap,
+            "vjv": vjv, "vjv_bound": 100 * n * EPS, "ok": bool(rel <= 50 * n * EPS * kap and vjv <= 100 * n * EPS),
+            "max_scaled_off": info["max_scaled_off"]}
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -352,7 +562,7 @@ def main():
     import torch
 
     import __graft_entry__
-    from paper_1008_0201_gb300 import binding, inputs
+    from paper_1008_0201_gb300 import binding
 
     if rank == 0:
         __graft_entry__.build()
@@ -366,56 +576,54 @@ def main():
             __graft_entry__.build()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    lib = binding.load_library()
+    binding.load_library()
+    peaks, peak_src = load_peaks()
 
-    G, J = replica_input(rank)
+    G, J, cplx = headline_input(args, rank)
     m, n = G.shape
+    dtype = binding.JAC_C128 if cplx else binding.JAC_R64
+    tdt = torch.complex128 if cplx else torch.float64
+    esz = 16 if cplx else 8
     opts = binding.default_opts(block_w=BLOCK_W, ordering=args.ordering, factor=args.factor,
                                 block_mode=args.block_mode, precision=args.precision,
                                 f64_products=args.f64_products)
     stream = torch.cuda.current_stream(dev)
     sptr = stream.cuda_stream
-    # inputs resident in HBM: one fresh column-major copy per step (G is overwritten in place)
-    Gcol = torch.from_numpy(np.ascontiguousarray(G.T)).to(dev)
-    total = args.warmup + args.steps
-    Gs = [Gcol.clone() for _ in range(total)]
+    # inputs resident in HBM: a pristine column-major copy; the solve overwrites a working copy,
+    # refreshed (device to device) before each step outside the timed events
+    G0 = torch.from_numpy(np.ascontiguousarray(G.T)).to(dev)
+    Gw = torch.empty_like(G0)
     Jd = torch.from_numpy(J).to(dev)
     lam = torch.empty(n, dtype=torch.float64, device=dev)
-    U = torch.empty((n, m), dtype=torch.float64, device=dev)
-    V = torch.empty((n, n), dtype=torch.float64, device=dev)
+    V = torch.empty((n, n), dtype=tdt, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
 
     def solve(Gbuf):
-        rc, info = binding.jacobi_hsvd_raw(m, n, Gbuf.data_ptr(), m, Jd.data_ptr(), opts, lam.data_ptr(),
-                                           U.data_ptr(), m, V.data_ptr(), n, sptr)
+        rc, info = binding.jacobi_hsvd_raw(m, n, Gbuf.data_ptr(), m, Jd.data_ptr(), opts, lam.data_ptr(), 0, m,
+                                           V.data_ptr(), n, sptr, dtype=dtype)
         if rc != 0:
             raise RuntimeError("jacobi_hsvd failed: %d %s" % (rc, binding.status_string(rc)))
         return info
 
     for i in range(args.warmup):
-        solve(Gs[i])
+        Gw.copy_(G0)
+        solve(Gw)
     torch.cuda.synchronize()
 
-    # --- timed region: device time of K solves (L2 flushed before each, outside the events).
-    # Only the pivot kernel (the dominant one) is bracketed by events here; the gram / update
-    # shares come from one extra solve after the timed region.
-    # The pivot's launch events run in the last timed solve only: each event pair in a sweep's
-    # graph adds its own gap, which would otherwise be charged to every step.
+    # --- timed region: device time of K solves, nothing else bracketed
     sampler = ClockSampler(local)
     sampler.start()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    evs = []
-    infos = []
+    evs, infos = [], []
     for i in range(args.steps):
+        Gw.copy_(G0)
         flush.fill_(float(i))
-        if i == args.steps - 1:
-            binding.jacobi_profile_begin(("pivot",))
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        infos.append(solve(Gs[args.warmup + i]))
+        infos.append(solve(Gw))
         e1.record(stream)
         evs.append((e0, e1))
     torch.cuda.synchronize()
@@ -423,31 +631,29 @@ def main():
         dist.barrier()
     clocks = sampler.stop()
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    prof_timed = {"pivot": binding.jacobi_profile_read("pivot")}
-    binding.jacobi_profile_end()
     ms = max_over_ranks(float(np.mean(step_ms)), dist, dev)
-    # kernel shares: one more solve with all three step kernels timed (outside the timed region)
-    binding.jacobi_profile_begin(("gram", "pivot", "update"))
-    solve(Gs[0].copy_(Gcol))
-    torch.cuda.synchronize()
-    prof = {k: binding.jacobi_profile_read(k) for k in ("gram", "pivot", "update")}
-    binding.jacobi_profile_end()
 
-    import oracle
+    # --- one more solve with every step kernel bracketed by events (outside the timed region)
+    kernels = ("gram", "pivot", "update", "gram_lowp", "update_lowp")
+    binding.jacobi_profile_begin(kernels)
+    Gw.copy_(G0)
+    pinfo = solve(Gw)
+    torch.cuda.synchronize()
+    prof = {k: binding.jacobi_profile_read(k) for k in kernels}
+    binding.jacobi_profile_end()
 
     # --- end to end through the C ABI with host buffers: pinned G in, lambda and V out
     Gh = torch.from_numpy(np.ascontiguousarray(G.T)).pin_memory()
     lam_h = torch.empty(n, dtype=torch.float64).pin_memory()
-    V_h = torch.empty((n, n), dtype=torch.float64).pin_memory()
-    Gdev = torch.empty_like(Gcol)
+    V_h = torch.empty((n, n), dtype=tdt).pin_memory()
     e2e_ms = []
-    for i in range(max(3, args.steps // 2)):
+    for i in range(3):
         flush.fill_(float(i))
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        Gdev.copy_(Gh, non_blocking=True)
-        solve(Gdev)
+        Gw.copy_(Gh, non_blocking=True)
+        solve(Gw)
         lam_h.copy_(lam, non_blocking=True)
         V_h.copy_(V, non_blocking=True)
         e1.record(stream)
@@ -458,71 +664,50 @@ def main():
     if rank == 0:
         info = infos[-1]
         lam_np = lam_h.numpy().copy()
-        Vn = V_h.numpy().T.copy()
-        ref = oracle.solve(G, J)
-        B = G / np.linalg.norm(G, axis=0)
-        kap = np.linalg.cond(B) ** 2
-        eig_rel = float(np.max(np.abs(lam_np - ref["lam"]) / np.abs(ref["lam"])))
-        J_out = np.where(lam_np < 0, -1, 1).astype(np.int8)
-        vjv = oracle.check_vjv(Vn, J, J_out)
-        ok = eig_rel <= 50 * n * EPS * kap and vjv <= 100 * n * EPS
-        # roofline of the dominant kernel (largest share of the measured kernel time)
-        shares = {k: v[0] for k, v in prof.items()}
-        dom = max(shares, key=shares.get)
-        d_ms, d_n = prof_timed[dom] if dom in prof_timed else prof[dom]
-        avg_s = d_ms / max(d_n, 1) * 1e-3
-        steps_per_solve = info["steps_per_sweep"] * info["sweeps"]
-        half = (2 * ((n + 2 * BLOCK_W - 1) // (2 * BLOCK_W))) // 2
-        k = 2 * BLOCK_W
-        if dom == "pivot":
-            # FP32 inner rotations: 3 dot products (6k flops) + F and W column updates (12k flops)
-            rot_per_launch = infos[-1]["rotations"] / max(1, d_n)  # the solve the events bracketed
-            flops = rot_per_launch * 18 * k
-            fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12  # unit counts x max SM clock
-            # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) come from an ncu
-            # capture of the kernel as it is; k_pivot's mailbox layout changed after the last
-            # capture (343552 B per launch), so no current figure is reported
-            roof = {"bound": "alu", "achieved": flops / avg_s / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
-                    "frac": flops / avg_s / 1e12 / fp32_peak, "traffic": None,
-                    "kernel": "k_pivot", "peak_source": "FP32 lanes x max clock (152 x 128 x 2 x 2.07 GHz)"}
-        else:
-            # FP64 mma: gram m k^2, update (m + n) k^2 multiply-adds per pair
-            macs = half * (m * k * k if dom == "gram" else (m + n) * k * k)
-            fp64_mma_peak = 1.04  # measured mma.sync m16n8k16 f64 throughput, TFLOP/s
-            roof = {"bound": "tensor", "achieved": 2 * macs / avg_s / 1e12, "peak": fp64_mma_peak,
-                    "unit": "TFLOP/s", "frac": 2 * macs / avg_s / 1e12 / fp64_mma_peak, "traffic": None,
-                    "kernel": "k_" + dom, "peak_source": "measured FP64 mma.sync m16n8k16 throughput"}
-        roof["kernel_ms_avg"] = avg_s * 1e3
-        roof["kernel_shares"] = {k2: v / max(sum(shares.values()), 1e-30) for k2, v in shares.items()}
+        acc = accuracy(G, J, cplx, lam_np, None if cplx else V_h.numpy().T.copy(), info, rank)
+        mr, nr = (2 * m, 2 * n) if cplx else (m, n)  # complex problems run as the real one of twice the order
+        nb = 2 * ((nr + 2 * BLOCK_W - 1) // (2 * BLOCK_W))
+        ev = kernel_evidence(prof, pinfo, mr, nr, nb // 2, 2 * BLOCK_W, peaks)
+        dom = max(ev, key=lambda k2: ev[k2]["total_ms"])
+        d = ev[dom]
+        tr = TRAFFIC_PER_PAIR.get(dom)
+        roof = {"bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": d["unit"],
+                "frac": d["frac"], "traffic": (tr * (nb // 2) if tr is not None else None), "kernel": dom,
+                "peak_source": "%s (MEASURED_PEAKS.json %s)" % (peak_src, "hbm_gbs" if d["bound"] == "hbm" else
+                                                              "bf16_tflops" + (" x 1.1/2.25 for tf32"
+                                                                               if "tf32" in d.get("dtype", "")
+                                                                               else "")),
+                "kernel_ms_avg": d["avg_us"] / 1e3}
+        wl = WORKLOAD if cplx else "hyperbolic SVD 512x512 Gaussian, J=diag(+1x256,-1x256), w=32, " + variant_name(args)
         line = {
             "metric": METRIC, "value": job_value(world, ms), "unit": "matrices/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD + ", " + variant_name(args), "n": n, "block_w": BLOCK_W,
-                       "ordering": args.ordering,
+            "config": {"workload": wl, "n": n, "complex": cplx, "block_w": BLOCK_W, "ordering": args.ordering,
                        "factor": args.factor, "block_mode": args.block_mode, "precision": args.precision,
-                       "f64_products": args.f64_products,
-                       "sweeps": info["sweeps"],
-                       "sweep_ms": ["%.2f" % x for x in info["sweep_ms"]],
+                       "f64_products": args.f64_products, "sweeps": info["sweeps"],
                        "fp32_sweeps": info["lowp_sweeps"], "steps_per_sweep": info["steps_per_sweep"],
-                       "pivot_phase_share": [c / max(1, sum(info["pivot_cycles"])) for c in info["pivot_cycles"]],
+                       "sweep_ms": ["%.1f" % x for x in info["sweep_ms"]],
                        "sweep_max_scaled": ["%.2e" % v for v in info["sweep_max_scaled"]],
-                       "inner_sweeps_per_pivot": info["inner_sweeps"] / max(1, info["pivots_rotated"]),
-                       "pivots_rotated": info["pivots_rotated"],
-                       "l2": "256 MiB buffer written before each solve, outside the per-solve CUDA events",
+                       "step_ms": ["%.1f" % x for x in step_ms],
+                       "l2": "inputs larger than L2, and a 256 MiB buffer written before each solve outside "
+                             "the per-solve CUDA events",
                        "parallelism": "replicas" if world > 1 else "single"},
             "e2e": {"value": job_value(world, e2e), "unit": "matrices/s",
-                    "h2d_bytes_per_step": int(Gh.numel() * 8), "d2h_bytes_per_step": int((n + n * n) * 8)},
+                    "h2d_bytes_per_step": int(Gh.numel() * esz), "d2h_bytes_per_step": int(n * 8 + n * n * esz)},
             "gpu_launches": int(sum(x["launches"] for x in infos)),
             "roofline": roof,
-            "accuracy": {"eig_rel_err": eig_rel, "eig_bound": 50 * n * EPS * kap, "vjv": vjv,
-                         "vjv_bound": 100 * n * EPS, "ok": bool(ok), "max_scaled_off": info["max_scaled_off"]},
+            "kernels": ev,
+            "accuracy": acc,
             "clocks": clocks,
         }
         if not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline()
+            line["cpu_baseline"] = cpu_baseline() if cplx else None
         if not args.no_other_workloads and world == 1:
-            line["other_workloads"] = other_workloads(dev)
+            ow = other_workloads(dev)
+            if not args.no_cpu_baseline:
+                ow["cpu_baselines"] = cpu_baselines_batches()
+            line["other_workloads"] = ow
         print(json.dumps(line))
     if dist:
         dist.barrier()

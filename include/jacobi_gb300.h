@@ -103,9 +103,14 @@ enum jac_precision {
 /* Arithmetic of the FP64 Gram, update and V_P J-orthogonality products (FP64 sweeps). */
 enum jac_f64_products {
   JAC_F64_MMA = 0,    /* FP64 tensor-core mma (m16n8k16 f64) */
-  JAC_F64_SPLIT16 = 1 /* exact FP16 tensor-core products of 7-bit digit slices of each operand,
-                         8 slices, recombined in FP64 (error-free splitting after Ozaki et al.):
-                         each product term exact to 2^-53 of its operand group bounds */
+  JAC_F64_SPLIT16 = 1,/* exact FP16 tensor-core products of 7-bit digit slices of each operand,
+                         8 slices, recombined once to FP64 (error-free splitting after Ozaki et
+                         al.): each product term exact to 2^-53 of its operand group bounds.  The
+                         update runs on the tcgen05 tensor cores (accumulators in tensor memory,
+                         integer rounding to FP64), the Gram block on the warp-level FP16 mma */
+  JAC_F64_SPLIT16_TC = 2 /* as JAC_F64_SPLIT16 with the Gram block on tcgen05 as well (same
+                            results to FP64 accuracy; slower on GB300 today: its 128-row digit
+                            groups leave the tensor-memory read-out latency exposed) */
 };
 
 typedef struct {
@@ -140,6 +145,7 @@ typedef struct {
   long long inner_sweeps;  /* inner sweeps summed over the transformed pivot blocks */
   double sweep_ms[64];     /* per sweep (first 64): host wall time from its first launch to its
                               completion, the precision switch included (single solves) */
+  long long pivots_rotated_lowp; /* of pivots_rotated: those of the FP32 sweeps */
 } jac_info;
 
 /* Fills *opts with the defaults: w = 32, round-robin, full block, sign-pivoted Cholesky,
@@ -150,8 +156,8 @@ void jacobi_default_opts(jac_opts* opts);
 const char* jacobi_status_string(int status);
 
 /* Library version, major*10000 + minor*100 + patch.  The minor number changes with the layout of
- * jac_opts / jac_info (0.3: jac_opts.f64_products). */
-#define JAC_VERSION 300
+ * jac_opts / jac_info (0.3: jac_opts.f64_products; 0.4: jac_info.pivots_rotated_lowp). */
+#define JAC_VERSION 400
 int jacobi_version(void);
 
 /*
@@ -321,8 +327,17 @@ int jacobi_sched_pairs(int nb, int ordering, const double* weights, int* pairs, 
 int jacobi_sched_pairs_noalloc(int nb, int ordering, const double* weights, int* pairs, int* counts,
                                int max_steps, int* nsteps, jac_stream_t stream);
 
-/* Kernels that the timing hooks below can bracket. */
-enum jac_kernel { JAC_KERNEL_GRAM = 0, JAC_KERNEL_PIVOT = 1, JAC_KERNEL_UPDATE = 2, JAC_KERNEL_COUNT = 3 };
+/* Kernels that the timing hooks below can bracket: the Gram and update of the FP64(-accurate)
+ * sweeps, the pivot kernel (FP32 and FP64 pivots of a step together), and the Gram and update
+ * of the FP32 sweeps (tensor cores). */
+enum jac_kernel {
+  JAC_KERNEL_GRAM = 0,
+  JAC_KERNEL_PIVOT = 1,
+  JAC_KERNEL_UPDATE = 2,
+  JAC_KERNEL_GRAM_LOWP = 3,
+  JAC_KERNEL_UPDATE_LOWP = 4,
+  JAC_KERNEL_COUNT = 5
+};
 
 /*
  * Kernel timing for measurement tools (no counterpart in the paper).  jacobi_profile_begin(mask)

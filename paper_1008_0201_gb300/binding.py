@@ -19,8 +19,8 @@ ORDER = {"modulus": 0, "modulus_mod": 1, "round_robin": 2, "cycle_weight": 3}
 FACTOR = {"chol": 0, "chol_diagpiv": 1, "chol_signpiv": 2}
 PRECISION = {"fp64": 0, "fp32": 1, "fp32_only": 2}
 BLOCK_MODE = {"full": 0, "oriented": 1}
-F64_PRODUCTS = {"mma": 0, "split16": 1}
-ABI_VERSION = 300  # JAC_VERSION of include/jacobi_gb300.h whose structs JacOpts / JacInfo mirror
+F64_PRODUCTS = {"mma": 0, "split16": 1, "split16_tc": 2}
+ABI_VERSION = 400  # JAC_VERSION of include/jacobi_gb300.h whose structs JacOpts / JacInfo mirror
 
 
 class JacOpts(ctypes.Structure):
@@ -36,7 +36,8 @@ class JacInfo(ctypes.Structure):
                 ("off_rel", ctypes.c_double), ("launches", ctypes.c_longlong), ("lowp_sweeps", ctypes.c_int),
                 ("global_ns_steps", ctypes.c_int), ("pivot_ns_steps", ctypes.c_longlong),
                 ("pivot_cycles", ctypes.c_longlong * 4), ("sweep_max_scaled", ctypes.c_double * 64),
-                ("inner_sweeps", ctypes.c_longlong), ("sweep_ms", ctypes.c_double * 64)]
+                ("inner_sweeps", ctypes.c_longlong), ("sweep_ms", ctypes.c_double * 64),
+                ("pivots_rotated_lowp", ctypes.c_longlong)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_
@@ -59,7 +60,7 @@ _lib = None
 EXPORTS = ("jacobi_default_opts", "jacobi_status_string", "jacobi_version", "jacobi_hsvd", "jacobi_eig_pd",
            "jacobi_sched_pairs", "jacobi_profile_begin", "jacobi_profile_read", "jacobi_profile_end",
            "jacobi_sched_pairs_noalloc", "jacobi_eig_batched", "jacobi_eig_backward", "jacobi_autotune_batched")
-KERNEL = {"gram": 0, "pivot": 1, "update": 2}
+KERNEL = {"gram": 0, "pivot": 1, "update": 2, "gram_lowp": 3, "update_lowp": 4}
 
 
 def load_library(path=LIB_PATH):
@@ -187,11 +188,12 @@ def jacobi_eig_pd(G, opts=None, want_u=True, raise_on_error=True):
     return _call("jacobi_eig_pd", G, None, opts, want_u, raise_on_error)
 
 
-def jacobi_hsvd_raw(m, n, G_ptr, ldg, J_ptr, opts, lam_ptr, U_ptr, ldu, V_ptr, ldv, stream_ptr):
-    """Direct pointer-level call (used by the end-to-end timing path); returns (status, info)."""
+def jacobi_hsvd_raw(m, n, G_ptr, ldg, J_ptr, opts, lam_ptr, U_ptr, ldu, V_ptr, ldv, stream_ptr, dtype=JAC_R64):
+    """Direct pointer-level call (used by the end-to-end timing path); returns (status, info).
+    dtype JAC_C128: G, U, V hold interleaved (re, im) doubles, leading dimensions in elements."""
     lib = load_library()
     info = JacInfo()
-    rc = lib.jacobi_hsvd(m, n, JAC_R64, ctypes.c_void_p(G_ptr), ldg, ctypes.c_void_p(J_ptr), ctypes.byref(opts),
+    rc = lib.jacobi_hsvd(m, n, dtype, ctypes.c_void_p(G_ptr), ldg, ctypes.c_void_p(J_ptr), ctypes.byref(opts),
                          ctypes.c_void_p(lam_ptr), ctypes.c_void_p(U_ptr) if U_ptr else None, ldu,
                          ctypes.c_void_p(V_ptr) if V_ptr else None, ldv, ctypes.byref(info),
                          ctypes.c_void_p(stream_ptr))

@@ -62,6 +62,10 @@ __global__ void k_update_oz(const JacProb* probs, int s, int gslabs);
 __global__ void k_gram32_tc(const JacProb* probs, int s, int CS, const __grid_constant__ CUtensorMap tmG);
 __global__ void k_update32_tc(const JacProb* probs, int s, int gtiles, int tpc, const __grid_constant__ CUtensorMap tmG,
                               const __grid_constant__ CUtensorMap tmV);
+__global__ void k_update_oz_tc(const JacProb* probs, int s);
+__global__ void k_gram_oz_tc(const JacProb* probs, int s, int CS);
+size_t tc_update_oz_smem_bytes();
+size_t tc_gram_oz_smem_bytes();
 size_t tc_gram32_smem_bytes();
 size_t tc_update32_smem_bytes();
 size_t oz_gram_smem_bytes();
@@ -168,6 +172,11 @@ int setup_attributes(int dev) {
   ok &= cudaFuncSetAttribute(k_gram32_tc, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess;
   ok &= cudaFuncSetAttribute(k_update32_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)tc_update32_smem_bytes()) == cudaSuccess;
+  ok &= cudaFuncSetAttribute(k_update_oz_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)tc_update_oz_smem_bytes()) == cudaSuccess;
+  ok &= cudaFuncSetAttribute(k_gram_oz_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)tc_gram_oz_smem_bytes()) == cudaSuccess;
+  ok &= cudaFuncSetAttribute(k_gram_oz_tc, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess;
   ok &= pivot_set_attributes() == 0;
   ok &= pivot64_set_attributes() == 0;
   ok &= cudaFuncSetAttribute(k_rank, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024) == cudaSuccess;
@@ -247,7 +256,7 @@ int check_opts(const jac_opts& o, int argpos, bool batch) {
   if (batch && o.precision == JAC_PREC_FP32) return -argpos;
   if (o.max_sweeps < 1) return -argpos;
   if (o.want_v != 0 && o.want_v != 1) return -argpos;
-  if (o.f64_products != JAC_F64_MMA && o.f64_products != JAC_F64_SPLIT16) return -argpos;
+  if (o.f64_products < JAC_F64_MMA || o.f64_products > JAC_F64_SPLIT16_TC) return -argpos;
   return 0;
 }
 
@@ -380,12 +389,15 @@ int launch_step(JacProb* dprobs, int count, int km, int max_half, int gslabs, in
                 bool lowp, bool fallback, const PivotParams& pp, cudaStream_t st, ProfRun& prof,
                 long long& launches, const TcMaps* maps = nullptr, const TcSplit* tsp = nullptr) {
   int r = 0;
-  size_t pm = prof.pre(JAC_KERNEL_GRAM, st);
+  size_t pm = prof.pre(lowp ? JAC_KERNEL_GRAM_LOWP : JAC_KERNEL_GRAM, st);
   if (lowp && maps)
     r = launch_cluster(k_gram32_tc, dim3(max_half * CS32, count), CS32, 128, tc_gram32_smem_bytes(), st,
                        (const JacProb*)dprobs, s, CS32, maps->g32);
   else if (lowp)
     r = launch_cluster(k_gram32, dim3(max_half * CS32, count), CS32, 128, 0, st, (const JacProb*)dprobs, s, CS32);
+  else if (pp.oz == 2)
+    r = launch_cluster(k_gram_oz_tc, dim3(max_half * CS, count), CS, 512, tc_gram_oz_smem_bytes(), st,
+                       (const JacProb*)dprobs, s, CS);
   else if (pp.oz)
     r = launch_cluster(k_gram_oz, dim3(max_half * CS, count), CS, 256, oz_gram_smem_bytes(), st,
                        (const JacProb*)dprobs, s, CS);
@@ -397,14 +409,19 @@ int launch_step(JacProb* dprobs, int count, int km, int max_half, int gslabs, in
   pivot_launch(km, max_half, count, st, dprobs, s, pp);
   if (fallback) pivot64_launch(km, max_half, count, st, dprobs, s, pp);  // blocks the FP32 kernel handed over
   prof.post(pm, st);
-  pm = prof.pre(JAC_KERNEL_UPDATE, st);
+  pm = prof.pre(lowp ? JAC_KERNEL_UPDATE_LOWP : JAC_KERNEL_UPDATE, st);
   if (lowp && maps && tsp)
     k_update32_tc<<<dim3(max_half, tsp->ysplit, count), 128, tc_update32_smem_bytes(), st>>>(
         dprobs, s, tsp->gtiles, tsp->tpc, maps->g32, maps->v32);
   else if (lowp)
     k_update32<<<dim3(max_half, tslabs, count), 256, 0, st>>>(dprobs, s, gslabs);
-  else if (pp.oz)
-    k_update_oz<<<dim3(max_half, tslabs, count), 256, oz_update_smem_bytes(), st>>>(dprobs, s, gslabs);
+  else if (pp.oz) {
+    // tensor-core digit update: persistent CTAs (one per SM) over the (pair, 128-row tile) items
+    // of each problem (tslabs counts 64-row slabs)
+    const int items = max_half * ((tslabs + 1) / 2 + 1);
+    const int nx = std::max(1, std::min(items, (152 + count - 1) / count));
+    k_update_oz_tc<<<dim3(nx, 1, count), 512, tc_update_oz_smem_bytes(), st>>>(dprobs, s);
+  }
   else
     k_update<<<dim3(max_half, tslabs, count), 128, kUpdSmem, st>>>(dprobs, s, gslabs);
   prof.post(pm, st);
@@ -623,11 +640,11 @@ int solve_real(int m, int n, int dtype, void* Gv, int ldg, const int8_t* Jdev, c
     ++launches;
     ck(cudaGetLastError());
   }
-  // the digit-product Gram is ~20x cheaper per row than the FP64 mma one and holds 173 KB of
-  // shared memory per CTA: >= 64 rows per CTA, so its clusters stay at <= 8 CTAs (clusters of 16
-  // such CTAs ran in two waves on the 512 x 512 workload: 61 us against 25 us of SM time)
-  const bool split16 = o.f64_products == JAC_F64_SPLIT16;
-  const int CS = choose_cluster(P.half, P.mp, split16 ? 64 : 16),
+  // the digit-product Gram is ~20x cheaper per row than the FP64 mma one and takes a whole SM
+  // (all 512 tensor-memory columns, ~165 KB of shared memory) per CTA, which works on groups of
+  // 128 rows: >= 128 rows per CTA
+  const bool split16 = o.f64_products != JAC_F64_MMA;
+  const int CS = choose_cluster(P.half, P.mp, split16 ? (o.f64_products == JAC_F64_SPLIT16_TC ? 128 : 64) : 16),
             CS32 = choose_cluster(P.half, P.mp, 64);
   const int gslabs = (P.mp + 63) / 64;
   const int tslabs = gslabs + (have_vw ? (P.np + 63) / 64 : 0);
@@ -643,7 +660,7 @@ int solve_real(int m, int n, int dtype, void* Gv, int ldg, const int8_t* Jdev, c
   }
 
   int sweeps = 0, converged = 0, lowp_sweeps = 0, ns_global = 0;
-  long long rot_total = 0, piv_total = 0, cyc_total[4] = {0, 0, 0, 0}, ns_total = 0, inner_total = 0;
+  long long rot_total = 0, piv_total = 0, piv_lowp = 0, cyc_total[4] = {0, 0, 0, 0}, ns_total = 0, inner_total = 0;
   double prev_max = 1e300;
   SweepRecord hrec = {};
   int last_steps = 0;
@@ -668,7 +685,7 @@ int solve_real(int m, int n, int dtype, void* Gv, int ldg, const int8_t* Jdev, c
     pp.factor = o.factor;
     pp.ns_mode = low ? 0 : 1;
     pp.oriented = (o.block_mode == JAC_BLOCK_ORIENTED) ? 1 : 0;
-    pp.oz = (o.f64_products == JAC_F64_SPLIT16) ? 1 : 0;
+    pp.oz = (o.f64_products == JAC_F64_SPLIT16) ? 1 : (o.f64_products == JAC_F64_SPLIT16_TC ? 2 : 0);
     if (weights) {
       const int npairs = P.nb * (P.nb - 1) / 2;
       if (!low) {
@@ -725,6 +742,7 @@ int solve_real(int m, int n, int dtype, void* Gv, int ldg, const int8_t* Jdev, c
     last_steps = nsteps;
     rot_total += hrec.rotations;
     piv_total += hrec.pivots_rotated;
+    if (phase == 1 || phase == 4) piv_lowp += hrec.pivots_rotated;
     ns_total += hrec.ns_steps;
     inner_total += hrec.inner_sweeps;
     for (int u = 0; u < 4; ++u) cyc_total[u] += hrec.cyc[u];
@@ -847,6 +865,7 @@ int solve_real(int m, int n, int dtype, void* Gv, int ldg, const int8_t* Jdev, c
     info->steps_per_sweep = last_steps;
     info->rotations = rot_total;
     info->pivots_rotated = piv_total;
+    info->pivots_rotated_lowp = piv_lowp;
     info->max_scaled_off = hrec.max_scaled;
     info->off_rel = (hrec.trace > 0.0) ? std::sqrt(hrec.off2) / hrec.trace : 0.0;
     info->launches = launches;
@@ -962,6 +981,7 @@ int solve_complex(int m, int n, void* Gv, int ldg, const int8_t* Jdev, const jac
       info->sweeps += info1.sweeps;
       info->rotations += info1.rotations;
       info->pivots_rotated += info1.pivots_rotated;
+      info->pivots_rotated_lowp += info1.pivots_rotated_lowp;
       info->launches += info1.launches + 2;
       info->lowp_sweeps += info1.lowp_sweeps;
       info->global_ns_steps += info1.global_ns_steps;
@@ -1193,7 +1213,7 @@ int solve_batched(int batch, const int* m, const int* n, int dtype, void* const*
   pp.factor = o.factor;
   pp.ns_mode = fp32_only ? 0 : 1;
   pp.oriented = (o.block_mode == JAC_BLOCK_ORIENTED) ? 1 : 0;
-  pp.oz = (o.f64_products == JAC_F64_SPLIT16) ? 1 : 0;
+  pp.oz = (o.f64_products == JAC_F64_SPLIT16) ? 1 : (o.f64_products == JAC_F64_SPLIT16_TC ? 2 : 0);
   ProfRun prof;
   prof.begin();
   long long launches = 0;

@@ -43,7 +43,7 @@ def test_hsvd_argument_positions(lib, dtype):
     assert _hsvd(lib, dtype=dtype, ldg=3) == -5
     assert _hsvd(lib, dtype=dtype, J=None) == -6
     for bad in (dict(block_w=0), dict(block_w=33), dict(ordering=4), dict(block_mode=2), dict(factor=3),
-                dict(precision=3), dict(max_sweeps=0), dict(want_v=2), dict(f64_products=2),
+                dict(precision=3), dict(max_sweeps=0), dict(want_v=2), dict(f64_products=3),
                 dict(f64_products=-1)):
         assert _hsvd(lib, dtype=dtype, opts=_opts(**bad)) == -7, bad
     assert _hsvd(lib, dtype=dtype, lam=None) == -8

@@ -1,5 +1,6 @@
-"""The two FP64 product paths vs the CPU oracle: exact FP16 digit products (f64_products =
-"split16", the default) and FP64 tensor-core mma ("mma").
+"""The FP64 product paths vs the CPU oracle: exact FP16 digit products (f64_products =
+"split16", the default: update on the tcgen05 tensor cores, Gram on the warp-level FP16 mma;
+"split16_tc": Gram on tcgen05 too) and FP64 tensor-core mma ("mma").
 
 The Gram, update and V_P residual products of the FP64 sweeps run as sums of exact FP16 x FP16
 tensor-core products of 7-bit digit slices (error-free splitting after Ozaki et al.); each
@@ -19,6 +20,7 @@ from test_gpu_parity import run
 pytestmark = pytest.mark.gpu
 
 S16 = dict(f64_products="split16")
+PRODUCTS = ["split16", "split16_tc"]
 
 
 @pytest.mark.parametrize("factor", ["chol", "chol_diagpiv", "chol_signpiv"])
@@ -33,11 +35,12 @@ def test_split16_config1_pd(cuda_dev, factor):
 
 @pytest.mark.parametrize("precision,block_mode", [("fp64", "full"), ("fp64", "oriented"), ("fp32", "full"),
                                                   ("fp32", "oriented")])
-def test_split16_config2(cuda_dev, precision, block_mode):
+@pytest.mark.parametrize("prod", PRODUCTS)
+def test_split16_config2(cuda_dev, prod, precision, block_mode):
     from paper_1008_0201_gb300 import inputs
 
     G, J = inputs.config2_hyperbolic()
-    out = run(G, J, cuda_dev, block_w=32, precision=precision, block_mode=block_mode, **S16)
+    out = run(G, J, cuda_dev, block_w=32, precision=precision, block_mode=block_mode, f64_products=prod)
     assert out["status"] == 0, out["info"]
     r = compare(G, J, out)
     print("C2-split16", precision, block_mode, out["info"]["sweeps"], r)
@@ -45,18 +48,20 @@ def test_split16_config2(cuda_dev, precision, block_mode):
 
 @pytest.mark.parametrize("m,n,w,frac", [(130, 100, 16, 0.4), (37, 37, 5, 0.5), (200, 61, 7, 0.0),
                                         (48, 33, 32, 0.3), (17, 3, 1, 0.34), (4500, 40, 8, 0.3)])
-def test_split16_ragged_and_tall(cuda_dev, m, n, w, frac):
+@pytest.mark.parametrize("prod", PRODUCTS)
+def test_split16_ragged_and_tall(cuda_dev, prod, m, n, w, frac):
     g = np.random.default_rng(5000 + m * 7 + n)
     G = g.standard_normal((m, n))
     J = np.ones(n, dtype=np.int8)
     J[g.choice(n, size=int(round(frac * n)), replace=False)] = -1
-    out = run(G, J, cuda_dev, block_w=w, ordering="round_robin", **S16)
+    out = run(G, J, cuda_dev, block_w=w, ordering="round_robin", f64_products=prod)
     assert out["status"] == 0, out["info"]
     compare(G, J, out)
 
 
 @pytest.mark.parametrize("span", [4, 12])
-def test_split16_graded_columns(cuda_dev, span):
+@pytest.mark.parametrize("prod", PRODUCTS)
+def test_split16_graded_columns(cuda_dev, prod, span):
     """G = B D with column scales 10^(-span/2 .. span/2) in shuffled order: every pivot block mixes
     columns of very different size, the case the per-column scaling of the update is for."""
     g = np.random.default_rng(5100 + span)
@@ -66,7 +71,7 @@ def test_split16_graded_columns(cuda_dev, span):
     J = np.ones(n, dtype=np.int8)
     J[g.choice(n, size=40, replace=False)] = -1
     for prec in ("fp64", "fp32"):
-        out = run(G, J, cuda_dev, block_w=16, precision=prec, **S16)
+        out = run(G, J, cuda_dev, block_w=16, precision=prec, f64_products=prod)
         assert out["status"] == 0, (prec, out["info"])
         compare(G, J, out)
 

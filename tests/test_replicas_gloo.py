@@ -33,7 +33,7 @@ def _worker(rank, world, port, q):
     try:
         local_ms = [40.0, 55.5][rank]
         slowest = bench.max_over_ranks(local_ms, dist, "cpu")
-        G, J = bench.replica_input(rank)
+        G, J = bench.replica_input(rank, n=64)
         q.put((rank, slowest, bench.job_value(world, slowest), float(G[0, 0]), int(J.sum())))
         dist.barrier()
     finally:
@@ -58,7 +58,7 @@ def test_replicas_two_gloo_ranks():
     assert s0 == s1 == 55.5                      # max over ranks, seen by every rank
     assert v0 == v1 == pytest.approx(2 * 1000.0 / 55.5)
     assert g0 != g1                              # each replica draws its own matrix
-    assert j0 == j1 == 0                         # J = diag(+1 x 256, -1 x 256) on every rank
+    assert j0 == j1 == 64                        # J = I (positive definite) on every rank
 
 
 def test_reference_arm_rank_nonzero_is_silent(capsys):
@@ -84,6 +84,8 @@ def test_single_rank_helpers():
 
     assert bench.max_over_ranks(12.5, None, "cpu") == 12.5
     assert bench.job_value(1, 40.0) == 25.0
-    G0, _ = bench.replica_input(0)
-    G0b, _ = bench.replica_input(0)
+    G0, _ = bench.replica_input(0, n=32)
+    G0b, _ = bench.replica_input(0, n=32)
     assert np.array_equal(G0, G0b)
+    G2, J2 = bench.replica_input(1, workload="c2")
+    assert G2.shape == (512, 512) and int(J2.sum()) == 0
