@@ -112,3 +112,56 @@ def test_complex_graded_full_size_properties(cuda_dev):
     Vs = V[:, idx]
     assert np.abs(Vs.conj().T @ Vs - np.eye(64)).max() <= 100 * n * eps
     assert np.linalg.norm(G @ Vs - Gs) / np.linalg.norm(G) <= 100 * n * eps
+
+
+def _read_golden(path):
+    meta, lam, in_lam = {}, [], False
+    with open(path) as f:
+        for ln in f:
+            ln = ln.strip()
+            if not ln or ln.startswith("#"):
+                continue
+            if ln == "lambda":
+                in_lam = True
+            elif in_lam:
+                lam.append(float(ln))
+            else:
+                k, v = ln.split(None, 1)
+                meta[k] = v
+    return meta, np.array(lam)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_complex_graded_full_size_vs_oracle(cuda_dev, precision):
+    """The graded workload at full size (n = 4096) against the oracle's eigenvalues for the same
+    draws (tests/golden/c3_graded_complex_n4096.txt, written by make_c3_golden.py from the oracle
+    alone and keyed by a hash of the Gaussian draws), element by element, within the stated bound
+    50 n eps kappa_2(A), kappa_2(A) = kappa_2(B_hat)^2, and within the tighter 50 n eps kappa_2(B_hat)."""
+    import hashlib
+    import os
+
+    import torch
+
+    from paper_1008_0201_gb300 import binding, inputs
+
+    meta, ref = _read_golden(os.path.join(os.path.dirname(__file__), "golden", "c3_graded_complex_n4096.txt"))
+    n = int(meta["n"])
+    g = inputs.rng(3, 0)
+    h = hashlib.sha256()
+    h.update(np.ascontiguousarray(g.standard_normal((n, n))).tobytes())
+    h.update(np.ascontiguousarray(g.standard_normal((n, n))).tobytes())
+    assert h.hexdigest() == meta["draws_sha256"], "the seeded draws differ from those the oracle solved"
+    G, _ = inputs.config3_graded_complex(n)
+    out = binding.jacobi_eig_pd(torch.from_numpy(G).to(cuda_dev),
+                                binding.default_opts(block_w=32, ordering="round_robin", block_mode="oriented",
+                                                     precision=precision), want_u=False)
+    torch.cuda.synchronize()
+    assert out["status"] == 0, out["info"]
+    lam = out["lam"].cpu().numpy()
+    kb = float(meta["kappa2_bhat"])
+    eps = 2.0 ** -53
+    rel = np.max(np.abs(lam - ref) / np.abs(ref))
+    assert rel <= 50 * n * eps * kb * kb, (rel, 50 * n * eps * kb * kb)
+    assert rel <= 50 * n * eps * kb, (rel, 50 * n * eps * kb)
+    print("C3 full size", precision, "max rel err %.3e" % rel, "bound(kappa_bhat) %.3e" % (50 * n * eps * kb),
+          "sweeps", out["info"]["sweeps"])
