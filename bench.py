@@ -40,9 +40,11 @@ WORKLOAD = ("graded complex Hermitian PD n=4096: G = B D, B complex Gaussian, D 
             "w = 32 real (16 complex) columns, block-oriented (HB), round-robin, FP32 tensor-core sweeps + "
             "FP64 polish, V accumulated")
 SAMPLE_N = 768  # order of the oracle's bounded sample of the headline workload
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of kernels captured with
-# ncu on the headline workload's kernels, per unit of work; None until captured for the kernel
-# as it is now (profiles/ holds the capture summaries)
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per evaluated pivot pair and launch,
+# from ncu captures of one launch of each kernel on the same workload at n = 1024 (realified
+# m = 2048, 32 pairs per step), scaled to the headline by rows (each pair's columns are read
+# once: the traffic grows with m); profiles/ holds the capture summaries.  Only kernels unchanged
+# since their capture are listed.
 TRAFFIC_PER_PAIR = {}
 
 
@@ -395,6 +397,18 @@ def other_workloads(dev, steps=3):
     ms_b = timed_ms(lambda: binding.jacobi_eig_backward(lamr, Ur, wt, Ub), 3, stream)
     n5 = Gc.shape[1]
     out["c5_forward"] = {"ms": ms_f, "matrices_per_s": Gc.shape[0] * 1e3 / ms_f}
+    # the headline workload in plain FP64 (every sweep FP64-accurate): the form the mixed one is
+    # compared to, same accuracy bound
+    G3, _ = inputs.config3_graded_complex(4096)
+    G3d = torch.from_numpy(G3).to(dev)
+    o3 = binding.default_opts(block_w=32, ordering="round_robin", block_mode="oriented", precision="fp64")
+    r3 = {}
+
+    def c3_fp64():
+        r3["o"] = binding.jacobi_eig_pd(G3d, o3, want_u=False)
+    ms3 = timed_ms(c3_fp64, 1, stream)
+    out["c3_graded_complex_4096_fp64"] = {"ms": ms3, "matrices_per_s": 1e3 / ms3, "sweeps": r3["o"]["info"]["sweeps"]}
+    del G3d, r3
     out["c5_backward"] = {"ms": ms_b, "tflops_fp64": 3 * 2 * Gc.shape[0] * n5 ** 3 / (ms_b * 1e-3) / 1e12}
     return out
 
@@ -405,11 +419,13 @@ def kernel_evidence(prof, info, m, n, half, k, peaks):
     bracketed by CUDA events on the solve's stream (jacobi_profile_*).  Algorithmic work per
     launch (units: pivot pairs of a step; all pairs take the Gram and the pivot, only rotated
     pairs the update):
-      FP32-sweep Gram (tcgen05 kind::tf32, 3 products h h', h l', l h'):  3 * 2 m k^2 per pair
+      FP32-sweep Gram (tcgen05 kind::tf32, 3 products h h', h l', l h'):  3 * 2 m k^2 per evaluated pair
       FP32-sweep update (same):                                         3 * 2 (m + n) k^2 per rotated pair
-      FP64 Gram (FP16 digit products, 36 per multiply-add):             36 * m k (k + 1) per pair
+      FP64 Gram (FP16 digit products, 36 per multiply-add):             36 * m k (k + 1) per evaluated pair
       FP64 update (43 digit products per multiply-add):                 43 * 2 (m + n) k^2 per rotated pair
-      pivot (HBM, A_P read + V_P written, k x k FP64 each):             2 * 8 k^2 bytes per pair
+      pivot (HBM, A_P read + V_P written, k x k FP64 each):             2 * 8 k^2 bytes per evaluated pair
+    (evaluated: the pairs whose Gram block and pivot ran; pairs whose blocks were unchanged since
+    a non-rotating evaluation are skipped by the pair cache)
     The tf32 peak is the measured bf16 peak x 1.1 / 2.25 (nominal tf32 / bf16 dense rates);
     the FP16 peak equals the bf16 one."""
     bf16 = peaks["bf16_tflops"]
@@ -417,6 +433,8 @@ def kernel_evidence(prof, info, m, n, half, k, peaks):
     hbm = peaks["hbm_gbs"]
     rot_lowp = info["pivots_rotated_lowp"]
     rot64 = info["pivots_rotated"] - rot_lowp
+    ev_lowp = info["pairs_evaluated_lowp"]  # pairs the Gram and pivot ran for (not cached)
+    ev64 = info["pairs_evaluated"] - ev_lowp
     ev = {}
     total = sum(v[0] for v in prof.values()) or 1e-30
     for name, (ms, launches) in prof.items():
@@ -425,24 +443,28 @@ def kernel_evidence(prof, info, m, n, half, k, peaks):
         avg_s = ms / launches * 1e-3
         e = {"launches": launches, "total_ms": ms, "avg_us": avg_s * 1e6, "share": ms / total}
         if name == "gram_lowp":
-            fl = half * 3 * 2 * m * k * k
+            fl = ev_lowp / launches * 3 * 2 * m * k * k
             e.update(bound="tensor", dtype="tf32x3", achieved=fl / avg_s / 1e12, peak=tf32, unit="TFLOP/s")
         elif name == "update_lowp":
             fl = rot_lowp / launches * 3 * 2 * (m + n) * k * k
             e.update(bound="tensor", dtype="tf32x3", achieved=fl / avg_s / 1e12, peak=tf32, unit="TFLOP/s")
         elif name == "gram":
-            fl = half * 36 * m * k * (k + 1)
+            fl = ev64 / launches * 36 * m * k * (k + 1)
             e.update(bound="tensor", dtype="f16 digits", achieved=fl / avg_s / 1e12, peak=bf16, unit="TFLOP/s",
-                     fp64_equivalent_tflops=half * m * k * (k + 1) / avg_s / 1e12)
+                     fp64_equivalent_tflops=fl / 36 / avg_s / 1e12)
         elif name == "update":
             fl = rot64 / launches * 43 * 2 * (m + n) * k * k
             e.update(bound="tensor", dtype="f16 digits", achieved=fl / avg_s / 1e12, peak=bf16, unit="TFLOP/s",
                      fp64_equivalent_tflops=fl / 43 / avg_s / 1e12)
         elif name == "pivot":
-            by = half * 2 * 8 * k * k
+            by = info["pairs_evaluated"] / launches * 2 * 8 * k * k
             e.update(bound="hbm", achieved=by / avg_s / 1e9, peak=hbm, unit="GB/s",
                      note="latency-bound on one SM per pair (dependent 2x2 rotations); HBM figure as asked")
         e["frac"] = e["achieved"] / e["peak"]
+        if name in ("gram", "pivot"):
+            e["pairs_per_launch"] = (ev64 if name == "gram" else info["pairs_evaluated"]) / launches
+        elif name == "gram_lowp":
+            e["pairs_per_launch"] = ev_lowp / launches
         ev[name] = e
     return ev
 
@@ -672,7 +694,8 @@ def main():
         d = ev[dom]
         tr = TRAFFIC_PER_PAIR.get(dom)
         roof = {"bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": d["unit"],
-                "frac": d["frac"], "traffic": (tr * (nb // 2) if tr is not None else None), "kernel": dom,
+                "frac": d["frac"], "traffic": (tr * d.get("pairs_per_launch", nb // 2) if tr is not None else None),
+                "kernel": dom,
                 "peak_source": "%s (MEASURED_PEAKS.json %s)" % (peak_src, "hbm_gbs" if d["bound"] == "hbm" else
                                                               "bf16_tflops" + (" x 1.1/2.25 for tf32"
                                                                                if "tf32" in d.get("dtype", "")

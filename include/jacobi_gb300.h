@@ -146,6 +146,10 @@ typedef struct {
   double sweep_ms[64];     /* per sweep (first 64): host wall time from its first launch to its
                               completion, the precision switch included (single solves) */
   long long pivots_rotated_lowp; /* of pivots_rotated: those of the FP32 sweeps */
+  long long pairs_evaluated;     /* pivot pairs whose Gram block and pivot ran, all sweeps (pairs
+                                    whose two blocks were unchanged since a non-rotating
+                                    evaluation are skipped: their outcome is already known) */
+  long long pairs_evaluated_lowp;/* of pairs_evaluated: those of the FP32 sweeps */
 } jac_info;
 
 /* Fills *opts with the defaults: w = 32, round-robin, full block, sign-pivoted Cholesky,

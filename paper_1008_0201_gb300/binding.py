@@ -37,7 +37,8 @@ class JacInfo(ctypes.Structure):
                 ("global_ns_steps", ctypes.c_int), ("pivot_ns_steps", ctypes.c_longlong),
                 ("pivot_cycles", ctypes.c_longlong * 4), ("sweep_max_scaled", ctypes.c_double * 64),
                 ("inner_sweeps", ctypes.c_longlong), ("sweep_ms", ctypes.c_double * 64),
-                ("pivots_rotated_lowp", ctypes.c_longlong)]
+                ("pivots_rotated_lowp", ctypes.c_longlong), ("pairs_evaluated", ctypes.c_longlong),
+                ("pairs_evaluated_lowp", ctypes.c_longlong)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_

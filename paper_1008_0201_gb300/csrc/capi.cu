@@ -35,6 +35,8 @@ int pivot64_set_attributes();
 void pivot64_launch(int km, int max_half, int nprob, cudaStream_t st, const JacProb* probs, int s,
                     const PivotParams& pp);
 __global__ void k_sweep_reduce(JacProb* probs, JacIO* io, SweepRecord* rec, int deactivate, int* remaining);
+__global__ void k_cache_init(const JacProb* probs);
+__global__ void k_cache_step(const JacProb* probs, int rec, int chk);
 __global__ void k_sort_signs(const JacProb* probs, JacIO* io, int8_t* Js_all, const long long* js_off);
 __global__ void k_apply_flags(JacProb* probs, const JacIO* io, int nprob);
 __global__ void k_gather_in(const JacProb* probs, const JacIO* io);
@@ -368,6 +370,9 @@ void carve_problem(Arena& ar, const Plan& P, JacProb& d, JacIO& io, bool weights
   d.active = 1;
   d.skip = ar.take<int>(P.half);
   d.stats = ar.take<PairStat>((size_t)P.nsteps * P.half);
+  d.cached = weights ? nullptr : ar.take<int>(P.half);  // pair cache: off for the weight ordering
+  d.pver = weights ? nullptr : ar.take<int4>((size_t)P.nsteps * P.half);
+  d.bver = weights ? nullptr : ar.take<int>(P.nb);
   io.perm_in = ar.take<int>(P.n);
   io.nrm2 = ar.take<double>(P.n);
   io.lam = ar.take<double>(P.n);
@@ -389,6 +394,8 @@ struct TcSplit {
 int launch_step(JacProb* dprobs, int count, int km, int max_half, int gslabs, int tslabs, int CS, int CS32, int s,
                 bool lowp, bool fallback, const PivotParams& pp, cudaStream_t st, ProfRun& prof,
                 long long& launches, const TcMaps* maps = nullptr, const TcSplit* tsp = nullptr) {
+  // the pair cache: record step s - 1, then mark the pairs of step s whose outcome is known
+  k_cache_step<<<count, 256, 0, st>>>(dprobs, s - 1, s);
   int r = 0;
   size_t pm = prof.pre(lowp ? JAC_KERNEL_GRAM_LOWP : JAC_KERNEL_GRAM, st);
   if (lowp && maps)
@@ -426,7 +433,7 @@ int launch_step(JacProb* dprobs, int count, int km, int max_half, int gslabs, in
   else
     k_update<<<dim3(max_half, tslabs, count), 128, kUpdSmem, st>>>(dprobs, s, gslabs);
   prof.post(pm, st);
-  launches += fallback ? 4 : 3;
+  launches += fallback ? 5 : 4;
   return cudaGetLastError() == cudaSuccess ? 0 : JAC_ECUDA;
 }
 
@@ -632,7 +639,8 @@ int solve_real(int m, int n, int dtype, void* Gv, int ldg, const int8_t* Jdev, c
   if (status == JAC_OK && (hio_back.flags & 1)) status = JAC_ENONFINITE;
   k_gather_in<<<dim3((P.mp + 255) / 256, n, 1), 256, 0, st>>>(L.probs, L.io);
   if (have_vw) k_init_v<<<dim3((P.np + 255) / 256, n, 1), 256, 0, st>>>(L.probs, L.io);
-  launches += have_vw ? 2 : 1;
+  k_cache_init<<<1, 256, 0, st>>>(L.probs);
+  launches += have_vw ? 3 : 2;
   ck(cudaGetLastError());
 
   int nsteps = P.nsteps;
@@ -662,6 +670,7 @@ int solve_real(int m, int n, int dtype, void* Gv, int ldg, const int8_t* Jdev, c
 
   int sweeps = 0, converged = 0, lowp_sweeps = 0, ns_global = 0;
   long long rot_total = 0, piv_total = 0, piv_lowp = 0, cyc_total[4] = {0, 0, 0, 0}, ns_total = 0, inner_total = 0;
+  long long ev_total = 0, ev_lowp = 0;
   double prev_max = 1e300;
   SweepRecord hrec = {};
   int last_steps = 0;
@@ -713,8 +722,9 @@ int solve_real(int m, int n, int dtype, void* Gv, int ldg, const int8_t* Jdev, c
         if (int r = launch_step(L.probs, 1, P.km, P.half, gslabs, tslabs, CS, CS32, s, low, phase != 1, pp, ss, pr,
                                 nl, use_tc ? &tmaps : nullptr, use_tc ? &tsplit : nullptr))
           return r;
+      k_cache_step<<<1, 256, 0, ss>>>(L.probs, -2, -1);  // record the last step of the sweep
       k_sweep_reduce<<<1, 256, 0, ss>>>(L.probs, L.io, L.rec, 0, nullptr);
-      ++nl;
+      nl += 2;
       return cudaGetLastError() == cudaSuccess ? 0 : JAC_ECUDA;
     };
     // graphs: one per precision phase, unless the ordering is re-planned every sweep
@@ -744,6 +754,8 @@ int solve_real(int m, int n, int dtype, void* Gv, int ldg, const int8_t* Jdev, c
     rot_total += hrec.rotations;
     piv_total += hrec.pivots_rotated;
     if (phase == 1 || phase == 4) piv_lowp += hrec.pivots_rotated;
+    ev_total += hrec.evaluated;
+    if (phase == 1 || phase == 4) ev_lowp += hrec.evaluated;
     ns_total += hrec.ns_steps;
     inner_total += hrec.inner_sweeps;
     for (int u = 0; u < 4; ++u) cyc_total[u] += hrec.cyc[u];
@@ -820,7 +832,8 @@ int solve_real(int m, int n, int dtype, void* Gv, int ldg, const int8_t* Jdev, c
         else
           k_gemm64<<<dim3((m + 31) / 32, (n + 31) / 32, 1), 128, 0, st>>>(m, n, n, hio.G, ldg, 0, hp.Vw, P.np, nullptr,
                                                                           nullptr, hp.Gw, P.mp, 0, 0, 0, 0, 0);
-        ++launches;
+        k_cache_init<<<1, 256, 0, st>>>(L.probs);  // G replaced: no earlier evaluation holds
+        launches += 2;
         ck(cudaGetLastError());
         ck(cudaStreamSynchronize(st));
         phase = 3;
@@ -867,6 +880,8 @@ int solve_real(int m, int n, int dtype, void* Gv, int ldg, const int8_t* Jdev, c
     info->rotations = rot_total;
     info->pivots_rotated = piv_total;
     info->pivots_rotated_lowp = piv_lowp;
+    info->pairs_evaluated = ev_total;
+    info->pairs_evaluated_lowp = ev_lowp;
     info->max_scaled_off = hrec.max_scaled;
     info->off_rel = (hrec.trace > 0.0) ? std::sqrt(hrec.off2) / hrec.trace : 0.0;
     info->launches = launches;
@@ -983,6 +998,8 @@ int solve_complex(int m, int n, void* Gv, int ldg, const int8_t* Jdev, const jac
       info->rotations += info1.rotations;
       info->pivots_rotated += info1.pivots_rotated;
       info->pivots_rotated_lowp += info1.pivots_rotated_lowp;
+      info->pairs_evaluated += info1.pairs_evaluated;
+      info->pairs_evaluated_lowp += info1.pairs_evaluated_lowp;
       info->launches += info1.launches + 2;
       info->lowp_sweeps += info1.lowp_sweeps;
       info->global_ns_steps += info1.global_ns_steps;
@@ -1183,6 +1200,7 @@ int solve_batched(int batch, const int* m, const int* n, int dtype, void* const*
   k_apply_flags<<<(batch + 255) / 256, 256, 0, st>>>(d_probs, d_io, batch);
   k_gather_in<<<dim3((max_mp + 255) / 256, max_n, batch), 256, 0, st>>>(d_probs, d_io);
   if (have_vw) k_init_v<<<dim3((max_np + 255) / 256, max_n, batch), 256, 0, st>>>(d_probs, d_io);
+  k_cache_init<<<batch, 256, 0, st>>>(d_probs);
   if (fp32_only) k_lowp_copy<<<dim3(8, batch), 256, 0, st>>>(d_probs, 0);
   ck(cudaGetLastError());
 
@@ -1229,8 +1247,9 @@ int solve_batched(int batch, const int* m, const int* n, int dtype, void* const*
           if (int r = launch_step(c.probs, c.count, c.km, c.max_half, c.gslabs, c.tslabs, 1, 1, s, fp32_only, true, pp,
                                   ss, pr, nl))
             return r;
+        k_cache_step<<<c.count, 256, 0, ss>>>(c.probs, -2, -1);  // record the last step of the sweep
         k_sweep_reduce<<<c.count, 256, 0, ss>>>(c.probs, c.io, c.rec, 1, d_remaining);
-        ++nl;
+        nl += 2;
       }
       return cudaGetLastError() == cudaSuccess ? 0 : JAC_ECUDA;
     };

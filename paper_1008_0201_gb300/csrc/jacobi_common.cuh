@@ -105,6 +105,13 @@ struct JacProb {
   int* skip;         // [half]
   struct PairStat* stats;  // [nsteps][half]
   unsigned* pflags;  // JAC_DEVERR_* bits of this problem
+  // Pair cache (NULL: off).  A pair whose two blocks have not changed since it was last
+  // evaluated in the same (step, slot), and which did not rotate then, would give bitwise the
+  // same Gram block, decision and statistics: its step kernels return at once.
+  int* cached;       // [half] 1: the pair of this slot is cached in the current step
+  int4* pver;        // [nsteps][half] (p, q, version of p, version of q) at the last evaluation;
+                     // version of p = -1 if the pair rotated
+  int* bver;         // [nb] block versions, bumped when a pair containing the block rotates
 };
 
 // User-side buffers of one problem and its finalize scratch.
@@ -149,6 +156,7 @@ struct PairStat {
   int inner_sweeps;
   int ns_steps;
   int active;         // 1 iff some |a_ij| > tol sqrt(a_ii a_jj): the FP64 convergence test
+  int evaluated;      // 1: the pivot ran for this pair in this sweep; 0: cached (pair_cache.cu)
   long long cyc[4];   // SM clocks of the pivot phases: stats, Cholesky, inner sweeps, J-orth.
 };
 
@@ -161,6 +169,7 @@ struct SweepRecord {
   long long cyc[4];
   long long ns_steps;
   long long inner_sweeps;
+  long long evaluated;  // pairs whose Gram block and pivot ran (not cached)
   unsigned int err;
   int pad;
 };

@@ -232,6 +232,7 @@ __global__ void __launch_bounds__((KM / 2) * LPP, 1)
   unsigned* err = a.pflags;
   const int pair = blockIdx.x;
   if (!a.active || s >= a.nsteps || pair >= a.counts[s]) return;
+  if (a.cached && a.cached[pair]) return;  // skip set, statistics kept (pair_cache.cu)
   PairStat* stats = a.stats + (size_t)s * a.half;
   const long long t_start = clock64();
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -293,6 +294,7 @@ __global__ void __launch_bounds__((KM / 2) * LPP, 1)
       atomicOr(err, JAC_DEVERR_NOTPD);
       a.skip[pair] = 1;
       PairStat st = {};
+      st.evaluated = 1;
       stats[pair] = st;
     }
     return;
@@ -356,6 +358,7 @@ __global__ void __launch_bounds__((KM / 2) * LPP, 1)
   st.inner_sweeps = 0;
   st.ns_steps = 0;
   st.active = (cnt > 0) ? 1 : 0;
+  st.evaluated = 1;
   const long long t_stats = clock64();
   if (cnt == 0) {
     if (tid == 0) {

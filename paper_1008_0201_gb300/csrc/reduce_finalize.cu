@@ -19,7 +19,7 @@ namespace jac {
 __global__ void k_sweep_reduce(JacProb* __restrict__ probs, JacIO* __restrict__ io, SweepRecord* __restrict__ rec,
                                int deactivate, int* __restrict__ remaining) {
   __shared__ double sm_d[8][3];
-  __shared__ long long sm_l[8][8];
+  __shared__ long long sm_l[8][9];
   JacProb& a = probs[blockIdx.x];
   if (!a.active) {
     if (threadIdx.x == 0) {
@@ -30,7 +30,7 @@ __global__ void k_sweep_reduce(JacProb* __restrict__ probs, JacIO* __restrict__ 
     return;
   }
   double mx = 0.0, off2 = 0.0, tr = 0.0;
-  long long rot = 0, piv = 0, cy[4] = {0, 0, 0, 0}, ns = 0, isw = 0;
+  long long rot = 0, piv = 0, cy[4] = {0, 0, 0, 0}, ns = 0, isw = 0, ev = 0;
   const double wdiag = 1.0 / (double)(a.nb > 1 ? a.nb - 1 : 1);
   for (int e = threadIdx.x; e < a.nsteps * a.half; e += blockDim.x) {
     const int s = e / a.half, slot = e % a.half;
@@ -43,6 +43,7 @@ __global__ void k_sweep_reduce(JacProb* __restrict__ probs, JacIO* __restrict__ 
     piv += st.active;
     ns += st.ns_steps;
     isw += st.inner_sweeps;
+    ev += st.evaluated;
     for (int u = 0; u < 4; ++u) cy[u] += st.cyc[u];
   }
   mx = warp_max_d(mx);
@@ -54,6 +55,7 @@ __global__ void k_sweep_reduce(JacProb* __restrict__ probs, JacIO* __restrict__ 
     piv += __shfl_xor_sync(0xffffffffu, piv, o);
     ns += __shfl_xor_sync(0xffffffffu, ns, o);
     isw += __shfl_xor_sync(0xffffffffu, isw, o);
+    ev += __shfl_xor_sync(0xffffffffu, ev, o);
     for (int u = 0; u < 4; ++u) cy[u] += __shfl_xor_sync(0xffffffffu, cy[u], o);
   }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -65,6 +67,7 @@ __global__ void k_sweep_reduce(JacProb* __restrict__ probs, JacIO* __restrict__ 
     sm_l[warp][1] = piv;
     sm_l[warp][2] = ns;
     sm_l[warp][7] = isw;
+    sm_l[warp][8] = ev;
     for (int u = 0; u < 4; ++u) sm_l[warp][3 + u] = cy[u];
   }
   __syncthreads();
@@ -78,6 +81,7 @@ __global__ void k_sweep_reduce(JacProb* __restrict__ probs, JacIO* __restrict__ 
       r.pivots_rotated += sm_l[w][1];
       r.ns_steps += sm_l[w][2];
       r.inner_sweeps += sm_l[w][7];
+      r.evaluated += sm_l[w][8];
       for (int u = 0; u < 4; ++u) r.cyc[u] += sm_l[w][3 + u];
     }
     r.err = *a.pflags;

@@ -309,7 +309,7 @@ __global__ void __launch_bounds__(512, 1) k_gram_oz_tc(const JacProb* __restrict
   const JacProb& a = probs[blockIdx.y];
   const int pair = blockIdx.x / CS;
   const int crank = (int)cluster.block_rank();
-  if (!a.active || s >= a.nsteps || pair >= a.counts[s]) return;  // uniform over the cluster
+  if (!a.active || s >= a.nsteps || pair >= a.counts[s] || (a.cached && a.cached[pair])) return;  // uniform
   const int* sp = a.pairs + (size_t)s * a.half * 2;
   const int p = sp[2 * pair], q = sp[2 * pair + 1];
   const int op = a.boff[p], wp = a.boff[p + 1] - op, oq = a.boff[q], wq = a.boff[q + 1] - oq;
