@@ -349,9 +349,9 @@ def other_workloads(dev, steps=3):
         return run
 
     ms64_default = timed_ms(batched("fp64"), 2, stream)
-    rules64 = binding.jacobi_autotune_batched(count=256, precision="fp64", device=dev)
+    rules64 = binding.jacobi_autotune_batched(count=2048, precision="fp64", device=dev)
     ms64 = timed_ms(batched("fp64"), 2, stream)
-    rules32 = binding.jacobi_autotune_batched(count=256, precision="fp32_only", device=dev)
+    rules32 = binding.jacobi_autotune_batched(count=2048, precision="fp32_only", device=dev)
     ms32 = timed_ms(batched("fp32_only"), 2, stream)
     binding.jacobi_autotune_batched(count=0, device=dev)
     show = lambda r: {"%d-%d" % (lo, hi): int(r[lo]) for lo, hi in ((8, 16), (17, 32), (33, 48), (49, 64),

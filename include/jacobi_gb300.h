@@ -273,14 +273,15 @@ int jacobi_eig_backward(int batch, int n, const double* lambda, long long s_lam,
 /*
  * jacobi_autotune_batched -- measures, on the current device, which block width makes
  * jacobi_eig_batched fastest for each size class of orders 8..128 (no counterpart in the paper;
- * Sec. 3 leaves the block width free).  For each class (8-16, 17-32, 33-48, 49-64, 65-96,
- * 97-128) it solves `count` synthetic problems drawn like the batched workload (orders spread
- * over the class, Gaussian entries, round(0.3 n) signs -1 at random positions) per candidate
- * rule, best of two timed runs, and keeps the fastest; a candidate replaces the class's default
- * only when it is at least 3% faster.  The candidates are one pivot block for the whole problem
- * (rule 0, n <= 64; the default up to 64) and fixed widths 8, 16 or 32 (32: the default above).
- * jacobi_eig_batched uses the measured rules on this device from then on.
- *  1 count       problems per class, 1..4096; 0 restores the default widths on this device
+ * Sec. 3 leaves the block width free).  It solves one synthetic batch of `count` problems drawn
+ * like the batched workload (orders spread evenly over 8..128, so that every class shares the
+ * launches as in a real batch; Gaussian entries; round(0.3 n) signs -1 at random positions) and
+ * goes through the classes (8-16, 17-32, 33-48, 49-64, 65-96, 97-128) in turn: a candidate rule
+ * replaces a class's current rule only when the whole batch, timed as the best of two runs, is
+ * at least 3% faster with it.  The candidates are one pivot block for the whole problem (rule 0,
+ * n <= 64; the default up to 64) and fixed widths 8, 16 or 32 (32: the default above 64).
+ * jacobi_eig_batched uses the chosen rules on this device from then on.
+ *  1 count       problems of the tuning batch, 1..4096; 0 restores the default widths on this device
  *  2 precision   JAC_PREC_FP64 or JAC_PREC_FP32_ONLY (the arithmetic to tune for)
  *  3 rules       host int[129] or NULL: the rule chosen for each order n (-1 outside 8..128)
  *  4 stream

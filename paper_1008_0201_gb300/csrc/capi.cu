@@ -1413,7 +1413,8 @@ int jacobi_autotune_batched(int count, int precision, int* rules, jac_stream_t s
   }
   if (count < 1 || count > 4096) return -1;
   if (precision != JAC_PREC_FP64 && precision != JAC_PREC_FP32_ONLY) return -2;
-  // size classes and the width rules tried in each (rule 0: one pivot block)
+  // size classes and the width rules tried in each (rule 0: one pivot block); the first rule of
+  // a class is its default (batch_width)
   struct Cls {
     int lo, hi;
     int rules[3];
@@ -1422,28 +1423,27 @@ int jacobi_autotune_batched(int count, int precision, int* rules, jac_stream_t s
                          {49, 64, {0, 16, 32}},    {65, 96, {32, 16, -1}},    {97, 128, {32, 16, -1}}};
   int best_rule[129];
   for (int n = 0; n <= 128; ++n) best_rule[n] = -1;
+  for (const Cls& c : classes)
+    for (int n = c.lo; n <= c.hi; ++n) best_rule[n] = c.rules[0];
   jac_opts o;
   jacobi_default_opts(&o);
   o.precision = precision;
   o.want_v = 1;
+  // one batch drawn like the batched workload: orders spread evenly over 8..128 (every class
+  // present, sharing launches as in a real batch), square, Gaussian entries, round(0.3 n) signs
+  // -1 at random positions of each problem
   std::vector<int> ms(count), ns(count), ld(count);
   std::vector<long long> offs(count + 1), joffs(count + 1);
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return JAC_ECUDA;
-  int status = JAC_OK;
-  unsigned long long seed = 0x5EED5EEDull;
-  for (const Cls& c : classes) {
-    // problems of the class drawn like the batched workload: orders spread evenly over [lo, hi],
-    // square, Gaussian entries, round(0.3 n) signs -1 at random positions of each problem
-    offs[0] = joffs[0] = 0;
-    for (int b = 0; b < count; ++b) {
-      ns[b] = ms[b] = ld[b] = c.lo + (int)(((long long)b * (c.hi - c.lo + 1)) / count);
-      offs[b + 1] = offs[b] + (long long)ns[b] * ns[b];
-      joffs[b + 1] = joffs[b] + ns[b];
-    }
-    std::vector<int8_t> hJ((size_t)joffs[count], 1);
+  offs[0] = joffs[0] = 0;
+  for (int b = 0; b < count; ++b) {
+    ns[b] = ms[b] = ld[b] = 8 + (int)(((long long)b * 121) / count);
+    offs[b + 1] = offs[b] + (long long)ns[b] * ns[b];
+    joffs[b + 1] = joffs[b] + ns[b];
+  }
+  std::vector<int8_t> hJ((size_t)joffs[count], 1);
+  {
     std::vector<int> idx;
-    unsigned long long lcg = seed * 0x9E3779B97F4A7C15ull + 1;
+    unsigned long long lcg = 0x5EED5EEDull;
     for (int b = 0; b < count; ++b) {  // partial Fisher-Yates shuffle of each problem's positions
       idx.resize(ns[b]);
       for (int i = 0; i < ns[b]; ++i) idx[i] = i;
@@ -1455,71 +1455,80 @@ int jacobi_autotune_batched(int count, int precision, int* rules, jac_stream_t s
         hJ[(size_t)(joffs[b] + idx[i])] = -1;
       }
     }
-    void* base = nullptr;
-    const size_t bytes = sizeof(double) * (3 * (size_t)offs[count] + (size_t)joffs[count]) + (size_t)joffs[count] + 256;
-    if (cudaMallocAsync(&base, bytes, st) != cudaSuccess) {
-      cudaGetLastError();
-      status = JAC_ENOMEM;
-      break;
-    }
-    double* G0 = static_cast<double*>(base);
-    double* Gw = G0 + offs[count];
-    double* Vb = Gw + offs[count];
-    double* lam = Vb + offs[count];
-    int8_t* Jb = reinterpret_cast<int8_t*>(lam + joffs[count]);
-    k_fill_gauss<<<1024, 256, 0, st>>>(G0, offs[count], seed++);
-    cudaMemcpyAsync(Jb, hJ.data(), hJ.size(), cudaMemcpyHostToDevice, st);
-    std::vector<void*> pG(count), pV(count);
-    std::vector<double*> pl(count);
-    std::vector<const int8_t*> pJ(count);
-    for (int b = 0; b < count; ++b) {
-      pG[b] = Gw + offs[b];
-      pV[b] = Vb + offs[b];
-      pl[b] = lam + joffs[b];
-      pJ[b] = Jb + joffs[b];
-    }
-    float best_ms = 1e30f, def_ms = 1e30f;
-    int best = -1;
-    const int def_rule = (c.hi <= 64) ? 0 : 32;  // the default width of the class (batch_width)
-    for (int r : c.rules) {
-      if (r < 0) continue;
-      if (r == 0 && c.hi > 64) continue;
-      {
-        std::lock_guard<std::mutex> lk(g_tune_mutex);
-        if (!g_tune_init) {
-          for (int d = 0; d < 64; ++d)
-            for (int n = 0; n <= 128; ++n) g_tuned_rule[d][n] = -1;
-          g_tune_init = true;
-        }
-        for (int n = c.lo; n <= c.hi; ++n) g_tuned_rule[dev][n] = r;  // candidate in force
-      }
-      float t = 1e30f;
-      for (int rep = 0; rep < 3 && status == JAC_OK; ++rep) {  // first run warms up; best of two
-        cudaMemcpyAsync(Gw, G0, sizeof(double) * offs[count], cudaMemcpyDeviceToDevice, st);
-        cudaEventRecord(e0, st);
-        const int rc = solve_batched(count, ms.data(), ns.data(), JAC_R64, pG.data(), ld.data(), pJ.data(), &o,
-                                     pl.data(), nullptr, nullptr, pV.data(), ld.data(), nullptr, st);
-        cudaEventRecord(e1, st);
-        if (rc < 0 || rc == JAC_ECUDA || rc == JAC_ENOMEM) status = (rc < 0) ? JAC_EINTERNAL : rc;
-        if (cudaEventSynchronize(e1) != cudaSuccess) status = JAC_ECUDA;
-        float tr = 0.0f;
-        cudaEventElapsedTime(&tr, e0, e1);
-        if (rep > 0) t = std::min(t, tr);
-      }
-      if (status != JAC_OK) break;
-      if (r == def_rule) def_ms = t;
-      if (t < best_ms) {
-        best_ms = t;
-        best = r;
-      }
-    }
-    // a rule replaces the default only when it is clearly faster (3%: above run-to-run noise)
-    if (best != def_rule && def_ms < 1e29f && best_ms > 0.97f * def_ms) best = def_rule;
-    cudaFreeAsync(base, st);
-    cudaStreamSynchronize(st);
-    if (status != JAC_OK) break;
-    for (int n = c.lo; n <= c.hi; ++n) best_rule[n] = best;
   }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return JAC_ECUDA;
+  int status = JAC_OK;
+  void* base = nullptr;
+  const size_t bytes = sizeof(double) * (3 * (size_t)offs[count] + (size_t)joffs[count]) + (size_t)joffs[count] + 256;
+  if (cudaMallocAsync(&base, bytes, st) != cudaSuccess) {
+    cudaGetLastError();
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return JAC_ENOMEM;
+  }
+  double* G0 = static_cast<double*>(base);
+  double* Gw = G0 + offs[count];
+  double* Vb = Gw + offs[count];
+  double* lam = Vb + offs[count];
+  int8_t* Jb = reinterpret_cast<int8_t*>(lam + joffs[count]);
+  k_fill_gauss<<<1024, 256, 0, st>>>(G0, offs[count], 0x5EED5EEDull);
+  cudaMemcpyAsync(Jb, hJ.data(), hJ.size(), cudaMemcpyHostToDevice, st);
+  std::vector<void*> pG(count), pV(count);
+  std::vector<double*> pl(count);
+  std::vector<const int8_t*> pJ(count);
+  for (int b = 0; b < count; ++b) {
+    pG[b] = Gw + offs[b];
+    pV[b] = Vb + offs[b];
+    pl[b] = lam + joffs[b];
+    pJ[b] = Jb + joffs[b];
+  }
+  // time of the whole batch under the given rules: best of two runs after a warm-up
+  auto time_rules = [&](const int* rule) -> float {
+    {
+      std::lock_guard<std::mutex> lk(g_tune_mutex);
+      if (!g_tune_init) {
+        for (int d = 0; d < 64; ++d)
+          for (int n = 0; n <= 128; ++n) g_tuned_rule[d][n] = -1;
+        g_tune_init = true;
+      }
+      for (int n = 0; n <= 128; ++n) g_tuned_rule[dev][n] = rule[n];
+    }
+    float t = 1e30f;
+    for (int rep = 0; rep < 3 && status == JAC_OK; ++rep) {
+      cudaMemcpyAsync(Gw, G0, sizeof(double) * offs[count], cudaMemcpyDeviceToDevice, st);
+      cudaEventRecord(e0, st);
+      const int rc = solve_batched(count, ms.data(), ns.data(), JAC_R64, pG.data(), ld.data(), pJ.data(), &o,
+                                   pl.data(), nullptr, nullptr, pV.data(), ld.data(), nullptr, st);
+      cudaEventRecord(e1, st);
+      if (rc < 0 || rc == JAC_ECUDA || rc == JAC_ENOMEM) status = (rc < 0) ? JAC_EINTERNAL : rc;
+      if (cudaEventSynchronize(e1) != cudaSuccess) status = JAC_ECUDA;
+      float tr = 0.0f;
+      cudaEventElapsedTime(&tr, e0, e1);
+      if (rep > 0) t = std::min(t, tr);
+    }
+    return t;
+  };
+  // coordinate descent over the classes: a candidate replaces a class's current rule only when
+  // the whole batch runs at least 3% faster with it (above run-to-run noise)
+  float best_ms = time_rules(best_rule);
+  for (const Cls& c : classes) {
+    if (status != JAC_OK) break;
+    for (int ri = 1; ri < 3 && status == JAC_OK; ++ri) {
+      const int r = c.rules[ri];
+      if (r < 0 || (r == 0 && c.hi > 64)) continue;
+      int trial[129];
+      for (int n = 0; n <= 128; ++n) trial[n] = best_rule[n];
+      for (int n = c.lo; n <= c.hi; ++n) trial[n] = r;
+      const float t = time_rules(trial);
+      if (status == JAC_OK && t < 0.97f * best_ms) {
+        best_ms = t;
+        for (int n = c.lo; n <= c.hi; ++n) best_rule[n] = r;
+      }
+    }
+  }
+  cudaFreeAsync(base, st);
+  cudaStreamSynchronize(st);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   {
