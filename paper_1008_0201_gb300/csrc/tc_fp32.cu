@@ -15,8 +15,9 @@
 //   loads two 32 x 32 boxes of G32 (columns op.. and oq.. of the pair; 128-byte swizzle), which
 //   are the K-major operand rows 0..63 (S); the threads write T = S - trunc(S) as rows 64..127.
 //   One MMA per 8 rows of K with A = B = [S; T] (M = N = 128) accumulates
-//   D = [S; T][S; T]^T, and A_P is the sum of its four 64 x 64 quadrants.  Four stages are in
-//   flight.  Partials of the cluster are added through distributed shared memory.
+//   D = [S; T][S; T]^T, and A_P is the sum of its four 64 x 64 quadrants.  Six stage buffers,
+//   loads four stages ahead (a refill waits for MMAs committed two stages earlier).  Partials
+//   of the cluster are added through distributed shared memory.
 // Update (k_update32_tc).  Grid (half, ysplit), 128 threads; a CTA takes consecutive 128-row
 //   tiles of G32 (then V32).  TMA stages the raw tile (rows contiguous: eight 32 x 32 boxes);
 //   tf32 operands must be K-major, so the threads transpose it into K-major h (X_h) and l
@@ -45,10 +46,12 @@ __device__ __forceinline__ int tc_slot(int c, int wp) { return c < wp ? c : 32 +
 }  // namespace
 
 // ------------------------------------------------------------------------------------ Gram
-#define TG_NS 4                                  // stages in flight
+#define TG_NS 6                                  // stage buffers
+#define TG_AHEAD (TG_NS - 2)                     // stages loaded ahead of the one consumed
 #define TG_STAGE 16384                           // S (p box, q box) + T, 128 rows x 128 B
 #define TG_CP_LD 65                              // partial row stride (floats)
-#define TG_SMEM (1024 + TG_NS * TG_STAGE + 64 * TG_CP_LD * 4 + 256)
+#define TG_P1 (128 * TG_CP_LD * 4)                // epilogue column-half sums, over the stages
+#define TG_SMEM (1024 + TG_NS * TG_STAGE + 256)      // partial Cp also over the stages (after P1)
 
 size_t tc_gram32_smem_bytes() { return TG_SMEM; }
 
@@ -56,8 +59,10 @@ __global__ void __launch_bounds__(128) k_gram32_tc(const JacProb* __restrict__ p
                                                    const __grid_constant__ CUtensorMap tmG) {
   extern __shared__ unsigned char tg_raw[];
   unsigned char* sm = align1k(tg_raw);
-  float* Cp = reinterpret_cast<float*>(sm + TG_NS * TG_STAGE);  // [64][TG_CP_LD] partial
-  uint64_t* full = reinterpret_cast<uint64_t*>(sm + TG_NS * TG_STAGE + 64 * TG_CP_LD * 4);
+  // [64][TG_CP_LD] partial, read by the cluster's CTAs after the main loop: it lives in the stage
+  // buffers (free by then), after the epilogue's P1
+  float* Cp = reinterpret_cast<float*>(sm + TG_P1);
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + TG_NS * TG_STAGE);
   uint64_t* done = full + TG_NS;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(done + TG_NS);
   cg::cluster_group cluster = cg::this_cluster();
@@ -95,13 +100,13 @@ __global__ void __launch_bounds__(128) k_gram32_tc(const JacProb* __restrict__ p
   bool bad = false;  // a bounded wait gave up (uniform after each block vote)
   int issued = 0;    // stages whose TMA loads thread 0 has issued
   if (tid == 0)
-    for (; issued < TG_NS - 1 && issued < nst; ++issued) issue(issued);
+    for (; issued < TG_AHEAD && issued < nst; ++issued) issue(issued);
   constexpr uint32_t idesc = tc::idesc_f32acc(tc::FMT_TF32, 128, 128, 0, 0);
   int i = 0;
   for (; i < nst; ++i) {
     const int slot = i % TG_NS;
     bool mine = false;
-    if (tid == 0 && issued < nst) {  // refill the slot that stage i - 1 used once its MMAs are done
+    if (tid == 0 && issued < nst) {  // refill the slot of stage i - 2 (its MMAs are done by now)
       const int j = issued;
       if (j >= TG_NS && !tc::mbar_wait(&done[j % TG_NS], ((j - TG_NS) / TG_NS) & 1)) mine = true;
       if (!mine) {
@@ -143,6 +148,7 @@ __global__ void __launch_bounds__(128) k_gram32_tc(const JacProb* __restrict__ p
     for (int j = i; j < issued; ++j) tc::mbar_wait(&full[j % TG_NS], (j / TG_NS) & 1);
     if (i > 0) tc::mbar_wait(&done[(i - 1) % TG_NS], ((i - 1) / TG_NS) & 1);
   }
+  __syncthreads();  // the stage buffers (P1, Cp below) are quiet
   tc::fence_after_sync();
   if (!bad && nst > 0) {
     // rows i and 64 + i, columns b and 64 + b of D: first the column halves per lane
@@ -246,20 +252,25 @@ __global__ void __launch_bounds__(128) k_update32_tc(const JacProb* __restrict__
   constexpr uint32_t idesc = tc::idesc_f32acc(tc::FMT_TF32, 128, 64, 0, 0);
   bool bad = false;
   int drain_tma = -1, drain_mma = -1;  // phases still in flight when a wait gave up
+  // the staged tile's load: issued for the first tile here, for each next one as soon as the
+  // current tile's MMAs (the last readers of the staged buffer) are done, so that it overlaps
+  // the current tile's epilogue
+  auto load_tile = [&](int t) {
+    const bool isg = t < gtiles;
+    const int r0 = (isg ? t : t - gtiles) * TU_ROWS;
+    tc::mbar_arrive_expect_tx(&bar[0], TU_X);
+    for (int cb = 0; cb < 2; ++cb)
+      for (int rb = 0; rb < 4; ++rb)
+        tc::tma_load_2d(Bst + cb * 16384 + rb * 4096, isg ? &tmG : &tmV, &bar[0], r0 + 32 * rb, cb ? oq : op);
+  };
+  if (tid == 0) load_tile(t_begin);
   for (int t = t_begin; t < t_end; ++t) {
     const int it = t - t_begin;
     const bool isg = t < gtiles;
-    const CUtensorMap* map = isg ? &tmG : &tmV;
     float* base = isg ? a.G32 : a.V32;
     const int ld = isg ? a.mp : a.np;
     const int r0 = (isg ? t : t - gtiles) * TU_ROWS;
     const int rows = min(TU_ROWS, (isg ? a.mp : a.np) - r0);
-    if (tid == 0) {  // the staged buffer is free: the previous tile's MMAs were waited for
-      tc::mbar_arrive_expect_tx(&bar[0], TU_X);
-      for (int cb = 0; cb < 2; ++cb)
-        for (int rb = 0; rb < 4; ++rb)
-          tc::tma_load_2d(Bst + cb * 16384 + rb * 4096, map, &bar[0], r0 + 32 * rb, cb ? oq : op);
-    }
     bool mine = !tc::mbar_wait(&bar[0], it & 1);
     // thread: row r = tid, all 64 columns; staged element (r, c) of box (rb, cb) is box row
     // c & 31, element r & 31
@@ -303,6 +314,7 @@ __global__ void __launch_bounds__(128) k_update32_tc(const JacProb* __restrict__
       break;
     }
     tc::fence_after_sync();
+    if (tid == 0 && t + 1 < t_end) load_tile(t + 1);  // the staged buffer is free again
     // epilogue: lane row 32 warp + lane, 64 columns -> the pair's columns of G32 / V32
     const int r = 32 * warp + lane;
 #pragma unroll
