@@ -41,11 +41,12 @@ WORKLOAD = ("graded complex Hermitian PD n=4096: G = B D, B complex Gaussian, D 
             "FP64 polish, V accumulated")
 SAMPLE_N = 768  # order of the oracle's bounded sample of the headline workload
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per evaluated pivot pair and launch,
-# from ncu captures of one launch of each kernel on the same workload at n = 1024 (realified
-# m = 2048, 32 pairs per step), scaled to the headline by rows (each pair's columns are read
-# once: the traffic grows with m); profiles/ holds the capture summaries.  Only kernels unchanged
-# since their capture are listed.
-TRAFFIC_PER_PAIR = {}
+# from ncu captures of one launch on the same workload at n = 1024 (realified m = 2048, 32 pairs
+# per step, every pair evaluated), scaled to the headline by rows (each pair's columns are read
+# once: the traffic grows with m).  Only kernels unchanged since their capture are listed.
+TRAFFIC_PER_PAIR = {
+    "gram": 33643008 / 32 * (8192 / 2048),  # k_gram_oz: profiles/digit_kernels_graded_complex_1024_ncu.md
+}
 
 
 def parse():
