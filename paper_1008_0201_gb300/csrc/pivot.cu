@@ -41,6 +41,7 @@ struct PivotSmem {
   static constexpr int P2 = KM / 2;    // pair slots
   static constexpr int MBS = 2 * KM + 8;  // mailbox slot: F and W column; +8 floats spreads banks
   static constexpr int LDD = KM + 8;   // digit rows of W (halves): 16-byte aligned, ldmatrix conflict-free
+  static constexpr int LDC = KM + 8;   // Cholesky rows (floats, in the mailboxes): 8 mod 32
   double V[KM * LDV];   // A_P first, then V (physical coordinates), FP64
   union {
     double M[KM * LDV];           // FP64 residual (FP64 mma products)
@@ -62,6 +63,7 @@ struct PivotSmem {
   int jphys[KM];
   int jloc[KM];
   float dg[2][KM];       // shifted Schur diagonal of the Cholesky steps (double-buffered)
+  unsigned pkey[2][KM];  // pivot search keys of the Cholesky steps (double-buffered)
   int pres[KM / 2];      // block-oriented cross step: columns of block p (pivot order) per slot
   int ptrav[KM / 2];     // ... and of block q
   float red_f[NW][4];
@@ -220,8 +222,10 @@ __device__ float oz_residual(PivotSmem<KM, LPP>& sm, const double* Vs, int k, in
   return mloc;
 }
 
+// KM = 32: four CTAs per SM (shared memory allows four; the register cap keeps them resident, no
+// spills), which the batched solves of many small pivots need; KM = 64: one CTA per SM
 template <int KM, int LPP>
-__global__ void __launch_bounds__((KM / 2) * LPP, 1)
+__global__ void __launch_bounds__((KM / 2) * LPP, KM == 32 ? 4 : 1)
     k_pivot(const JacProb* __restrict__ probs, int s, PivotParams pp) {
   using SM = PivotSmem<KM, LPP>;
   constexpr int NT = SM::NT, NW = SM::NW;
@@ -276,12 +280,14 @@ __global__ void __launch_bounds__((KM / 2) * LPP, 1)
     const double aii = Vs[tid * LDV + tid];
     if (!(aii > 0.0) || !(aii < 1.0e300)) atomicOr(&sm.bad, 1);
     const float d = sqrtf((float)aii);
-    const double id = 1.0 / (double)d;
+    const double d2 = (double)d * (double)d;  // exact
     sm.dd[tid] = d;
-    sm.fid[tid] = (float)id;
+    sm.fid[tid] = 1.0f / d;
     sm.perm[tid] = tid;
-    // e_ii = a_ii / d_i^2 - 1 in FP64 (cancellation), then rounded once
-    sm.S[tid * LDS + tid] = (float)(aii * id * id - 1.0);
+    // e_ii = a_ii / d_i^2 - 1 = (a_ii - d_i^2) / d_i^2: the difference is exact in FP64 (both
+    // agree to FP32 accuracy), so one FP32 division rounds the result (no FP64 division, whose
+    // latency is ~650 clocks on GB300)
+    sm.S[tid * LDS + tid] = (float)(aii - d2) / (float)d2;
     tr = aii;
   }
   for (int e = tid; e < KM * LDF; e += NT) {
@@ -376,53 +382,62 @@ __global__ void __launch_bounds__((KM / 2) * LPP, 1)
   for (int c = 0; c < k; ++c) npos += (sm.jloc[c] > 0) ? 1 : 0;  // J sorted: + block first
   __syncthreads();
   const bool signpiv = (pp.factor == 2), diagpiv = (pp.factor == 1);
-  // Right-looking Cholesky of I + E with diagonal pivoting inside the sign groups, on unpermuted
-  // storage: the trailing entry (a, b), a < b (local indices), stays at S[b * LDS + a]; the pivot
-  // of step i is perm[i]; row i of R~ - I is kept by column index in Fr; the shifted Schur
-  // diagonal s_cc is double-buffered in dg, so that every warp finds the same pivot from the
-  // buffer the previous step completed and one block barrier per step suffices.
-  float* Fr = sm.Vf;  // row i at Fr[i * LDS + c]
-  if (tid < k) sm.dg[0][tid] = sm.S[tid * LDS + tid];
-  // the strictly upper entries (rr, cx), rr < cx < KM, enumerated e = cx (cx - 1) / 2 + rr and
-  // dealt out EPT per thread: every step updates them with independent loads
-  constexpr int NPAIR = KM * (KM - 1) / 2, EPT = (NPAIR + NT - 1) / NT;
-  int ecx[EPT], err_[EPT];
-#pragma unroll
-  for (int t = 0; t < EPT; ++t) {
-    const int e = tid + t * NT;
-    int c = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)e)) * 0.5f);
-    while (c * (c - 1) / 2 > e) --c;
-    while ((c + 1) * c / 2 <= e) ++c;
-    ecx[t] = (e < NPAIR) ? c : KM;  // KM: no entry
-    err_[t] = e - c * (c - 1) / 2;
+  // Left-looking Cholesky of I + E with diagonal pivoting inside the sign groups, on unpermuted
+  // storage: the pivot of step i is perm[i]; row i of R~ - I is kept by column index in Fr (the
+  // scaled entries e_ab stay untouched in S).  Step i forms row i only: for every column c not
+  // yet pivoted, (e_pc - sum_{l<i} R~_lp R~_lc) / r_ii, the sum split over TPC lanes of one warp
+  // (rows l = t mod TPC) and combined by shuffles; the shifted Schur diagonal s_cc (dg) and the
+  // search key of the next step are updated by the column's own thread, both double-buffered,
+  // so one block barrier per step suffices.  Every step is a short dependent chain: the loads
+  // that do not depend on the pivot are issued before the key reduction, and the sum runs over
+  // all rows without predicates (rows >= i of Fr are zero; row i is written in step i only after
+  // the shuffles of the warp that reads it, so its products are 0).
+  constexpr int TPC = NT / KM, CPW = 32 / TPC, NU = KM / TPC, LDC = SM::LDC;
+  static_assert(TPC * KM == NT && CPW * TPC == 32 && NU % 4 == 0, "TPC lanes of one warp per column");
+  static_assert(2 * SM::P2 * SM::MBS >= KM * LDC, "Cholesky rows fit in the mailboxes");
+  float* Fr = &sm.mb[0][0];  // row i at Fr[i * LDC + c]; LDC = 8 mod 32: a warp's loads hit 32 banks
+  const int ct = lane / CPW, cc = warp * CPW + lane % CPW;  // share of the sum, column
+  const bool pivsel = signpiv || diagpiv;
+  // the key of column c for step i: the largest unscaled Schur diagonal d_c^2 (1 + s_cc) in the
+  // sign group of step i (sign pivoting, Algorithm 3.3) or among all remaining columns (diagonal
+  // pivoting, HFC), as the value's bits above the low 6 (order-preserving for v >= 0) and 63 - c,
+  // so that one warp max-reduction yields the largest value, ties to the smaller index
+  auto in_group = [&](int i, int c) { return c < k && (!signpiv || ((i < npos) ? (c < npos) : (c >= npos))); };
+  auto key_of = [&](float d2, float s, int c) {
+    const float v = fmaxf(d2 * (1.0f + s), 0.0f);
+    return (__float_as_uint(v) & 0xFFFFFFC0u) | (unsigned)(63 - c);
+  };
+  for (int e = tid; e < KM * LDC; e += NT) Fr[e] = 0.0f;
+  if (tid < KM) {
+    const float s0 = (tid < k) ? sm.S[tid * LDS + tid] : 0.0f;
+    sm.dg[0][tid] = s0;
+    sm.dg[1][tid] = s0;
+    sm.pkey[0][tid] = in_group(0, tid) ? key_of(sm.dd[tid] * sm.dd[tid], s0, tid) : 0u;
   }
-  bool live[EPT];  // entry t still in the trailing matrix
-#pragma unroll
-  for (int t = 0; t < EPT; ++t) live[t] = ecx[t] < k;
-  unsigned long long done = 0ull;  // columns already pivoted (identical in every thread)
+  const bool colk = cc < k;
+  const float ddc2 = colk ? sm.dd[cc] * sm.dd[cc] : 0.0f;
+  bool pivd = !colk;  // this thread's column pivoted already (or absent)
+  const float* fcol = Fr + ct * LDC + cc;
+  const float* frow = Fr + ct * LDC;
   __syncthreads();
   for (int i = 0; i < k; ++i) {
-    const float* dg = sm.dg[i & 1];
-    float* dgn = sm.dg[(i + 1) & 1];
+    // independent of the pivot
+    const int b = i & 1;
+    const float dgc = sm.dg[b][cc];
+    float fc[NU];
+#pragma unroll
+    for (int u = 0; u < NU; ++u) fc[u] = fcol[TPC * u * LDC];
     int p = i;
-    if (signpiv || diagpiv) {
-      // the largest unscaled Schur diagonal d_j^2 (1 + s_jj): in the sign group of step i
-      // (sign pivoting, Algorithm 3.3) or among all remaining columns (diagonal pivoting, HFC)
-      // key: the value's bits above the low 6 (order-preserving for v >= 0) and 63 - j, so one
-      // warp max-reduction yields the largest value, ties to the smaller index; every warp
-      // computes the same key
-      const int lo = (signpiv && i >= npos) ? npos : 0, hi = (signpiv && i < npos) ? npos : k;
-      unsigned key = 0u;
-      for (int j = lo + lane; j < hi; j += 32) {
-        if ((done >> j) & 1ull) continue;
-        const float dj = sm.dd[j];
-        const float v = fmaxf(dj * dj * (1.0f + dg[j]), 0.0f);
-        key = max(key, (__float_as_uint(v) & 0xFFFFFFC0u) | (unsigned)(63 - j));
-      }
-      key = __reduce_max_sync(0xffffffffu, key);
+    if (pivsel) {
+      const unsigned key = __reduce_max_sync(0xffffffffu, max(sm.pkey[b][lane], sm.pkey[b][lane + 32 < KM ? lane + 32 : lane]));
       p = 63 - (int)(key & 63u);
     }
-    const float sii = dg[p];
+    // dependent on the pivot
+    const float sii = sm.dg[b][p];
+    const float scp = sm.S[max(p, cc) * LDS + min(p, cc)];
+    float fp[NU];
+#pragma unroll
+    for (int u = 0; u < NU; ++u) fp[u] = frow[TPC * u * LDC + p];
     const float piv1 = 1.0f + sii;
     // The scaled Schur pivot is 1 / (A~^-1)_pp >= 1 / kappa(A~).  Below 64 eps_32 the column is
     // in the span of the previous ones at the precision of this factorization: the block goes
@@ -431,36 +446,34 @@ __global__ void __launch_bounds__((KM / 2) * LPP, 1)
       if (tid == 0) sm.bad = 1;
       break;  // uniform: every thread read the same pivot
     }
-    done |= 1ull << p;
+    pivd = pivd || (p == cc);
     const float rinv = rsqrtf(piv1);  // 1 / r
-    const float r = piv1 * rinv, ipiv = rinv * rinv;
-    // row i of R~ - I (by column index) and the Schur diagonal
-    if (tid < k && !((done >> tid) & 1ull)) {
-      const float spc = sm.S[max(p, tid) * LDS + min(p, tid)];
-      Fr[i * LDS + tid] = spc * rinv;
-      dgn[tid] = dg[tid] - spc * spc * ipiv;
+    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
+#pragma unroll
+    for (int u = 0; u < NU; u += 4) {
+      a0 = fmaf(fp[u], fc[u], a0);
+      a1 = fmaf(fp[u + 1], fc[u + 1], a1);
+      a2 = fmaf(fp[u + 2], fc[u + 2], a2);
+      a3 = fmaf(fp[u + 3], fc[u + 3], a3);
     }
-    if (tid == 0) {
-      Fr[i * LDS + p] = __fdividef(sii, 1.0f + r);
+    float dot = (a0 + a1) + (a2 + a3);
+#pragma unroll
+    for (int o = CPW; o < 32; o <<= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+    // row i of R~ - I (by column index), the Schur diagonal and the next step's key
+    const float v = (scp - dot) * rinv;
+    const float dn = fmaf(-v, v, dgc);
+    const unsigned nk = (!pivd && in_group(i + 1, cc)) ? key_of(ddc2, dn, cc) : 0u;
+    if (ct == 0) {
+      if (!pivd) {
+        Fr[i * LDC + cc] = v;
+        sm.dg[b ^ 1][cc] = dn;
+      }
+      sm.pkey[b ^ 1][cc] = nk;
+    } else if (ct == 1 && cc == 0) {
+      const float r = piv1 * rinv;
+      Fr[i * LDC + p] = __fdividef(sii, 1.0f + r);  // r - 1 without cancellation
       sm.perm[i] = p;
     }
-    // Schur complement of the strictly upper trailing entries; reads touch row p only, which
-    // this step does not write
-    // (all loads first, the old values included, then all stores: no load waits on a store)
-    float nv[EPT];
-    int adr[EPT];
-#pragma unroll
-    for (int t = 0; t < EPT; ++t) {
-      const int c = ecx[t], rr = err_[t];
-      live[t] = live[t] && c != p && rr != p;
-      const int cc = live[t] ? c : 0, rc = live[t] ? rr : 0;  // dead entries read row 0 (in bounds)
-      adr[t] = cc * LDS + rc;
-      const float a = sm.S[max(p, cc) * LDS + min(p, cc)], b = sm.S[max(p, rc) * LDS + min(p, rc)];
-      nv[t] = fmaf(-a * ipiv, b, sm.S[adr[t]]);
-    }
-#pragma unroll
-    for (int t = 0; t < EPT; ++t)
-      if (live[t]) sm.S[adr[t]] = nv[t];
     __syncthreads();
   }
   __syncthreads();
@@ -481,7 +494,7 @@ __global__ void __launch_bounds__((KM / 2) * LPP, 1)
     const int r = e % k, c = e / k;
     if (r <= c) {
       const int pc = sm.perm[c];
-      sm.F[c * LDF + r] = Fr[r * LDS + pc] * sm.dd[pc];
+      sm.F[c * LDF + r] = Fr[r * LDC + pc] * sm.dd[pc];
     }
   }
   float d_new = 0.0f;
@@ -582,6 +595,11 @@ __global__ void __launch_bounds__((KM / 2) * LPP, 1)
         // ---- rotate the pair (ci, cj) of this slot
         const bool act = (ci >= 0) && (cj >= 0);
         const int ii = act ? ci : 0, jj = act ? cj : 0;
+        // what does not depend on the dot product first
+        const float si = sm.dd[ii], sj = sm.dd[jj];
+        const bool trig = sm.jphys[ii] == sm.jphys[jj];
+        const float aii = fmaf(si, si, cni), ajj = fmaf(sj, sj, cnj);
+        const float rs = rsqrtf(aii) * rsqrtf(ajj);
         float sij = 0.0f;
 #pragma unroll
         for (int u = 0; u < R; ++u) sij = fmaf(fi[u], fj[u], sij);
@@ -589,53 +607,41 @@ __global__ void __launch_bounds__((KM / 2) * LPP, 1)
         const float fji = col_entry<R>(fj, ii, lane0);  // F_ij: row i of column j
         const float fij = col_entry<R>(fi, jj, lane0);  // F_ji
         if (act) {
-          const float si = sm.dd[ii], sj = sm.dd[jj];
           const float aij = si * fji + sj * fij + sij;
-          const float aii = fmaf(si, si, cni), ajj = fmaf(sj, sj, cnj);
           const float beta = fabsf(aij);
-          const float scaled = beta * rsqrtf(aii) * rsqrtf(ajj);
+          const float scaled = beta * rs;
           if (scaled > tol_in) {
             ++my_rot;
             my_max = fmaxf(my_max, scaled);
             const float e = (aij < 0.0f) ? -1.0f : 1.0f;
-            float q11, q12, q21, cm1, dci, dcj;
-            if (sm.jphys[ii] == sm.jphys[jj]) {
-              // trigonometric, Eq. (2.1): cot(2 phi) = (a_jj - a_ii) / (2 |a_ij|), i.e.
-              // t = sign(a_jj - a_ii) 2|a_ij| / (|a_jj - a_ii| + sqrt((a_jj - a_ii)^2 + 4|a_ij|^2)),
-              // evaluated after an exact power-of-two scaling of both terms into [1, 4)
-              const float num = (sj - si) * (sj + si) + (cnj - cni);
-              const float mxv = fmaxf(fabsf(num), 2.0f * beta);
-              const float sc = __int_as_float(0x7f000000 - (__float_as_int(mxv) & 0x7f800000));
-              const float nu = num * sc, b2 = 2.0f * beta * sc;
-              const float den = fabsf(nu) + sqrtf(fmaf(nu, nu, b2 * b2));
-              const float t = copysignf(__fdividef(b2, den), num);
-              const float c = rsqrtf(fmaf(t, t, 1.0f));
-              const float s_ = t * c;
-              q11 = c;
-              q12 = e * s_;
-              q21 = -e * s_;
-              cm1 = -__fdividef(s_ * s_, 1.0f + c);
-              dci = -t * beta;  // a_ii' = a_ii - t |a_ij|, a_jj' = a_jj + t |a_ij|
-              dcj = t * beta;
-            } else {
-              // hyperbolic: coth(2 phi) = -(a_ii + a_jj) / (2 |a_ij|), i.e.
-              // t = -2|a_ij| / (a_ii + a_jj + sqrt((a_ii + a_jj - 2|a_ij|)(a_ii + a_jj + 2|a_ij|))),
-              // with the |tanh| < 1 guard of Sec. 3.2
-              const float apd = aii + ajj;
-              const float sc = __int_as_float(0x7f000000 - (__float_as_int(apd) & 0x7f800000));
-              const float ap = apd * sc, b2 = 2.0f * beta * sc;
-              const float r2 = (ap - b2) * (ap + b2);
-              float t = (r2 > 0.0f) ? -__fdividef(b2, ap + sqrtf(r2)) : -1.0f;
-              if (!(fabsf(t) < 1.0f) || !((1.0f - t) * (1.0f + t) > 0.0f)) t = copysignf(0.9f, t);
-              const float ch = rsqrtf((1.0f - t) * (1.0f + t));
-              const float sh = t * ch;
-              q11 = ch;
-              q12 = e * sh;
-              q21 = e * sh;
-              cm1 = __fdividef(sh * sh, 1.0f + ch);
-              dci = t * beta;  // both diagonals move by t |a_ij| (the J-trace is invariant)
-              dcj = t * beta;
-            }
+            // One branch-free path for both kinds (sg = +1 trigonometric, -1 hyperbolic), so
+            // that the slots of a warp never split on the sign pattern:
+            //  trigonometric, Eq. (2.1): cot(2 phi) = (a_jj - a_ii) / (2 |a_ij|), i.e.
+            //    t = sign(x) 2|a_ij| / (|x| + sqrt(x^2 + 4|a_ij|^2)),  x = a_jj - a_ii;
+            //  hyperbolic: coth(2 phi) = -(a_ii + a_jj) / (2 |a_ij|), i.e.
+            //    t = -2|a_ij| / (x + sqrt((x - 2|a_ij|)(x + 2|a_ij|))),  x = a_ii + a_jj,
+            //    with the |tanh| < 1 guard of Sec. 3.2;
+            // both evaluated after an exact power-of-two scaling of x and 2|a_ij| into [1, 4).
+            // The square roots are x rsqrt(x): the angle needs FP32 accuracy only, the
+            // rotation built from it is orthogonal (J-orthogonal) whatever t is.
+            const float sg = trig ? 1.0f : -1.0f;
+            const float x = trig ? (sj - si) * (sj + si) + (cnj - cni) : aii + ajj;
+            const float mxv = fmaxf(fabsf(x), 2.0f * beta);
+            const float sc = __int_as_float(0x7f000000 - (__float_as_int(mxv) & 0x7f800000));
+            const float nu = x * sc, b2 = 2.0f * beta * sc;
+            const float rr = trig ? fmaf(nu, nu, b2 * b2) : (nu - b2) * (nu + b2);
+            const bool ok = rr > 0.0f;
+            const float root = ok ? rr * rsqrtf(rr) : 0.0f;
+            const float tm = __fdividef(b2, fabsf(nu) + root);
+            float t = trig ? copysignf(tm, x) : (ok ? -tm : -1.0f);
+            if (!trig && (!(fabsf(t) < 1.0f) || !((1.0f - t) * (1.0f + t) > 0.0f))) t = copysignf(0.9f, t);
+            const float c = rsqrtf(fmaf(sg * t, t, 1.0f));  // cos or cosh
+            const float s_ = t * c;                          // sin or sinh
+            const float q11 = c, q12 = e * s_, q21 = -sg * e * s_;
+            const float cm1 = -sg * __fdividef(s_ * s_, 1.0f + c);  // c - 1 without cancellation
+            // a_ii' = a_ii - t |a_ij|, a_jj' = a_jj + t |a_ij| (trigonometric); both move by
+            // t |a_ij| (hyperbolic: the J-trace is invariant)
+            const float dci = -sg * t * beta, dcj = t * beta;
             // F <- F Q + Dp (Q - I), Wd <- Wd Q + (Q - I): the Dp (Q - I) / (Q - I) terms touch
             // rows i and j only
 #pragma unroll
@@ -667,13 +673,37 @@ __global__ void __launch_bounds__((KM / 2) * LPP, 1)
         }
         // ---- pass one column on: the traveler round the ring, or at the end of the group's
         // ring its split (first half: traveler to slot + g/2, which sends back its resident)
-        if (st_ < g - 1 || g > g_last) {
-          const bool ring = st_ < g - 1;
-          const bool give_res = !ring && pos >= g / 2;  // second half of a split sends its resident
-          const int dst = ring ? base + ((pos + 1) & (g - 1)) : (pos < g / 2 ? slot + g / 2 : slot - g / 2);
-          // row l * R + u of a column sits at u * LPP + l of its mailbox slot: the 8 lanes of a
+        if (st_ < g - 1) {
+          // ring step (uniform over the block): the traveler goes to the next slot of the group.
+          // Row l * R + u of a column sits at u * LPP + l of its mailbox slot: the 8 lanes of a
           // slot write 32 consecutive bytes per u, and the 4 slots of a warp land on distinct
           // banks (lane-contiguous rows l * R + u put lanes l and l + 4 on the same banks)
+          const int dst = base + ((pos + 1) & (g - 1));
+          float* box = sm.mb[buf] + dst * MBS + l;
+#pragma unroll
+          for (int u = 0; u < R; ++u) {
+            box[u * LPP] = fj[u];
+            box[KM + u * LPP] = wj[u];
+          }
+          if (l == 0) {
+            sm.mphys[buf][dst] = cj;
+            sm.mcn[buf][dst] = cnj;
+          }
+          __syncthreads();
+          const float* in = sm.mb[buf] + slot * MBS + l;
+#pragma unroll
+          for (int u = 0; u < R; ++u) {
+            fj[u] = in[u * LPP];
+            wj[u] = in[KM + u * LPP];
+          }
+          cj = sm.mphys[buf][slot];
+          cnj = sm.mcn[buf][slot];
+          buf ^= 1;
+        } else if (g > g_last) {
+          // end of the group's ring: its split (first half: traveler to slot + g/2, which sends
+          // back its resident)
+          const bool give_res = pos >= g / 2;
+          const int dst = pos < g / 2 ? slot + g / 2 : slot - g / 2;
           float* box = sm.mb[buf] + dst * MBS + l;
 #pragma unroll
           for (int u = 0; u < R; ++u) {
