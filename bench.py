@@ -339,8 +339,8 @@ def other_workloads(dev, steps=3):
     ptr = lambda t, o, es: (np.uint64(t.data_ptr()) + o[:-1].astype(np.uint64) * np.uint64(es)).astype(np.uint64)
     last = {}
 
-    def batched(prec):
-        ob = binding.default_opts(precision=prec, want_v=1)
+    def batched(prec, fused=1):
+        ob = binding.default_opts(precision=prec, want_v=1, fused_step=fused)
 
         def run():
             Gw.copy_(G0)
@@ -353,7 +353,8 @@ def other_workloads(dev, steps=3):
     rules64 = binding.jacobi_autotune_batched(count=2048, precision="fp64", device=dev)
     ms64 = timed_ms(batched("fp64"), 2, stream)
     rules32 = binding.jacobi_autotune_batched(count=2048, precision="fp32_only", device=dev)
-    ms32 = timed_ms(batched("fp32_only"), 2, stream)
+    ms32_unfused = timed_ms(batched("fp32_only", fused=0), 2, stream)  # three kernels per step
+    ms32 = timed_ms(batched("fp32_only"), 2, stream)  # last: the statuses below are of this run
     binding.jacobi_autotune_batched(count=0, device=dev)
     show = lambda r: {"%d-%d" % (lo, hi): int(r[lo]) for lo, hi in ((8, 16), (17, 32), (33, 48), (49, 64),
                                                                       (65, 96), (97, 128))}
@@ -378,7 +379,8 @@ def other_workloads(dev, steps=3):
     out["c4_batched_fp64"] = {"ms": ms64, "matrices_per_s": len(Gs) * 1e3 / ms64, "width_rules": show(rules64),
                               "untuned_ms": ms64_default, "problem_status": statuses("fp64")}
     out["c4_batched_fp32_only"] = {"ms": ms32, "matrices_per_s": len(Gs) * 1e3 / ms32, "width_rules": show(rules32),
-                                   "problem_status": statuses("fp32_only")}
+                                   "problem_status": statuses("fp32_only"),
+                                   "unfused_ms": ms32_unfused}  # Gram, pivot, update as separate kernels
     out["c4_one_call_per_problem_fp64"] = {"sample": sample, "matrices_per_s": sample * 1e3 / msl}
     # C5: forward (batched, 256 problems of order 256) and the backward kernel
     Gc, w, C = inputs.config5_backward()

@@ -124,6 +124,10 @@ typedef struct {
   int want_v;      /* 1: accumulate and return V (n x n); 0: V is not touched */
   double tol;      /* rotate a pair (i,j) iff |a_ij| > tol sqrt(a_ii a_jj); <= 0 selects n*2^-53 */
   int f64_products;/* enum jac_f64_products */
+  int fused_step;  /* 1: the FP32 sweeps of small problems run Gram, pivot and update of a pair in
+                      one kernel (X_P read from and written to HBM once per step; m <= 96 rows for
+                      pivot blocks of k <= 32 columns, m <= 192 for k <= 64); 0: three kernels per
+                      step.  Same arithmetic either way (FP32 Gram and update products). */
 } jac_opts;
 
 typedef struct {
@@ -153,15 +157,17 @@ typedef struct {
 } jac_info;
 
 /* Fills *opts with the defaults: w = 32, round-robin, full block, sign-pivoted Cholesky,
- * FP64, max_sweeps = 50, want_v = 1, tol = n*2^-53 (tol <= 0), FP64 products JAC_F64_SPLIT16. */
+ * FP64, max_sweeps = 50, want_v = 1, tol = n*2^-53 (tol <= 0), FP64 products JAC_F64_SPLIT16,
+ * fused FP32 steps on. */
 void jacobi_default_opts(jac_opts* opts);
 
 /* Short text for a return code. */
 const char* jacobi_status_string(int status);
 
 /* Library version, major*10000 + minor*100 + patch.  The minor number changes with the layout of
- * jac_opts / jac_info (0.3: jac_opts.f64_products; 0.4: jac_info.pivots_rotated_lowp). */
-#define JAC_VERSION 400
+ * jac_opts / jac_info (0.3: jac_opts.f64_products; 0.4: jac_info.pivots_rotated_lowp;
+ * 0.5: jac_opts.fused_step). */
+#define JAC_VERSION 500
 int jacobi_version(void);
 
 /*
@@ -335,15 +341,19 @@ int jacobi_sched_pairs_noalloc(int nb, int ordering, const double* weights, int*
                                int max_steps, int* nsteps, jac_stream_t stream);
 
 /* Kernels that the timing hooks below can bracket: the Gram and update of the FP64(-accurate)
- * sweeps, the pivot kernel (FP32 and FP64 pivots of a step together), and the Gram and update
- * of the FP32 sweeps (tensor cores). */
+ * sweeps, the pivot kernel (FP32 and FP64 pivots of a step together), the Gram and update of the
+ * FP32 sweeps (tensor cores), and the fused FP32 step: Gram, pivot and update of a pair in one
+ * CTA, used in the FP32 sweeps when every problem of the launch has at most 96 rows of G (rows
+ * padded to 16; pivot blocks of k <= 32 columns) or 192 (k <= 64); the FP64 pivot of a block it
+ * hands over is counted with it. */
 enum jac_kernel {
   JAC_KERNEL_GRAM = 0,
   JAC_KERNEL_PIVOT = 1,
   JAC_KERNEL_UPDATE = 2,
   JAC_KERNEL_GRAM_LOWP = 3,
   JAC_KERNEL_UPDATE_LOWP = 4,
-  JAC_KERNEL_COUNT = 5
+  JAC_KERNEL_STEP_FUSED = 5,
+  JAC_KERNEL_COUNT = 6
 };
 
 /*

@@ -20,13 +20,14 @@ FACTOR = {"chol": 0, "chol_diagpiv": 1, "chol_signpiv": 2}
 PRECISION = {"fp64": 0, "fp32": 1, "fp32_only": 2}
 BLOCK_MODE = {"full": 0, "oriented": 1}
 F64_PRODUCTS = {"mma": 0, "split16": 1, "split16_tc": 2}
-ABI_VERSION = 400  # JAC_VERSION of include/jacobi_gb300.h whose structs JacOpts / JacInfo mirror
+ABI_VERSION = 500  # JAC_VERSION of include/jacobi_gb300.h whose structs JacOpts / JacInfo mirror
 
 
 class JacOpts(ctypes.Structure):
     _fields_ = [("block_w", ctypes.c_int), ("ordering", ctypes.c_int), ("block_mode", ctypes.c_int),
                 ("factor", ctypes.c_int), ("precision", ctypes.c_int), ("max_sweeps", ctypes.c_int),
-                ("want_v", ctypes.c_int), ("tol", ctypes.c_double), ("f64_products", ctypes.c_int)]
+                ("want_v", ctypes.c_int), ("tol", ctypes.c_double), ("f64_products", ctypes.c_int),
+                ("fused_step", ctypes.c_int)]
 
 
 class JacInfo(ctypes.Structure):
@@ -61,7 +62,7 @@ _lib = None
 EXPORTS = ("jacobi_default_opts", "jacobi_status_string", "jacobi_version", "jacobi_hsvd", "jacobi_eig_pd",
            "jacobi_sched_pairs", "jacobi_profile_begin", "jacobi_profile_read", "jacobi_profile_end",
            "jacobi_sched_pairs_noalloc", "jacobi_eig_batched", "jacobi_eig_backward", "jacobi_autotune_batched")
-KERNEL = {"gram": 0, "pivot": 1, "update": 2, "gram_lowp": 3, "update_lowp": 4}
+KERNEL = {"gram": 0, "pivot": 1, "update": 2, "gram_lowp": 3, "update_lowp": 4, "step_fused": 5}
 
 
 def load_library(path=LIB_PATH):

@@ -31,6 +31,9 @@ __global__ void k_gram32(const JacProb* probs, int s, int CS);
 __global__ void k_update32(const JacProb* probs, int s, int gslabs);
 int pivot_set_attributes();
 void pivot_launch(int km, int max_half, int nprob, cudaStream_t st, const JacProb* probs, int s, const PivotParams& pp);
+void fused_step_launch(int km, int max_half, int nprob, cudaStream_t st, const JacProb* probs, int s,
+                       const PivotParams& pp);
+int fused_step_max_rows(int km);
 int pivot64_set_attributes();
 void pivot64_launch(int km, int max_half, int nprob, cudaStream_t st, const JacProb* probs, int s,
                     const PivotParams& pp);
@@ -260,6 +263,7 @@ int check_opts(const jac_opts& o, int argpos, bool batch) {
   if (o.max_sweeps < 1) return -argpos;
   if (o.want_v != 0 && o.want_v != 1) return -argpos;
   if (o.f64_products < JAC_F64_MMA || o.f64_products > JAC_F64_SPLIT16_TC) return -argpos;
+  if (o.fused_step != 0 && o.fused_step != 1) return -argpos;
   return 0;
 }
 
@@ -393,10 +397,27 @@ struct TcSplit {
 
 int launch_step(JacProb* dprobs, int count, int km, int max_half, int gslabs, int tslabs, int CS, int CS32, int s,
                 bool lowp, bool fallback, const PivotParams& pp, cudaStream_t st, ProfRun& prof,
-                long long& launches, const TcMaps* maps = nullptr, const TcSplit* tsp = nullptr) {
+                long long& launches, const TcMaps* maps = nullptr, const TcSplit* tsp = nullptr,
+                bool fused = false) {
   // the pair cache: record step s - 1, then mark the pairs of step s whose outcome is known
   k_cache_step<<<count, 256, 0, st>>>(dprobs, s - 1, s);
   int r = 0;
+  if (lowp && fused) {
+    // FP32 sweep step of small problems: Gram, pivot and update of each pair in one CTA (pivot.cu,
+    // k_step_fused); a block it hands over takes the FP64 pivot, then the plain FP32 update,
+    // which acts only on those blocks (the fused kernel marks its own pairs done)
+    size_t pm = prof.pre(JAC_KERNEL_STEP_FUSED, st);
+    fused_step_launch(km, max_half, count, st, dprobs, s, pp);
+    if (fallback) pivot64_launch(km, max_half, count, st, dprobs, s, pp);
+    prof.post(pm, st);
+    if (fallback) {
+      pm = prof.pre(JAC_KERNEL_UPDATE_LOWP, st);
+      k_update32<<<dim3(max_half, tslabs, count), 256, 0, st>>>(dprobs, s, gslabs);
+      prof.post(pm, st);
+    }
+    launches += fallback ? 4 : 2;
+    return cudaGetLastError() == cudaSuccess ? 0 : JAC_ECUDA;
+  }
   size_t pm = prof.pre(lowp ? JAC_KERNEL_GRAM_LOWP : JAC_KERNEL_GRAM, st);
   if (lowp && maps)
     r = launch_cluster(k_gram32_tc, dim3(max_half * CS32, count), CS32, 128, tc_gram32_smem_bytes(), st,
@@ -661,6 +682,8 @@ int solve_real(int m, int n, int dtype, void* Gv, int ldg, const int8_t* Jdev, c
   // FP32 sweeps of the mixed mode stop at the scaled off-norm the FP32 Gram still resolves (its
   // entries carry errors ~ eps_32 sqrt(m) relative to ||g_i|| ||g_j||)
   const double tau_lo = std::max(o.tol, 8.0 * 5.9604644775390625e-08 * std::sqrt((double)m));
+  // FP32 sweeps of small problems: one fused kernel per step
+  const bool fused = o.fused_step == 1 && P.mp <= fused_step_max_rows(P.km);
   int phase = mixed ? 1 : (fp32_only ? 4 : 3);  // 1: FP32 sweeps of the mixed mode, 3: FP64, 4: FP32 only
   if (lowp && status == JAC_OK) {
     k_lowp_copy<<<dim3(ew_blocks, 1), 256, 0, st>>>(L.probs, 0);  // FP64 layout -> FP32 copies
@@ -720,7 +743,7 @@ int solve_real(int m, int n, int dtype, void* Gv, int ldg, const int8_t* Jdev, c
     auto record = [&](cudaStream_t ss, long long& nl, ProfRun& pr) -> int {
       for (int s = 0; s < nsteps; ++s)
         if (int r = launch_step(L.probs, 1, P.km, P.half, gslabs, tslabs, CS, CS32, s, low, phase != 1, pp, ss, pr,
-                                nl, use_tc ? &tmaps : nullptr, use_tc ? &tsplit : nullptr))
+                                nl, use_tc ? &tmaps : nullptr, use_tc ? &tsplit : nullptr, fused))
           return r;
       k_cache_step<<<1, 256, 0, ss>>>(L.probs, -2, -1);  // record the last step of the sweep
       k_sweep_reduce<<<1, 256, 0, ss>>>(L.probs, L.io, L.rec, 0, nullptr);
@@ -1208,14 +1231,15 @@ int solve_batched(int batch, const int* m, const int* n, int dtype, void* const*
     JacProb* probs;
     JacIO* io;
     SweepRecord* rec;
-    int count, km, max_half, max_steps, gslabs, tslabs;
+    int count, km, max_half, max_steps, gslabs, tslabs, max_mp;
   };
   std::vector<Cls> cls;
   auto add_cls = [&](int first, int count, int km) {
     if (count <= 0) return;
-    Cls c{d_probs + first, d_io + first, d_rec + first, count, km, 0, 0, 0, 0};
+    Cls c{d_probs + first, d_io + first, d_rec + first, count, km, 0, 0, 0, 0, 0};
     for (int i = first; i < first + count; ++i) {
       const Plan& P = plans[order[i]];
+      c.max_mp = std::max(c.max_mp, P.mp);
       c.max_half = std::max(c.max_half, P.half);
       c.max_steps = std::max(c.max_steps, P.nsteps);
       c.gslabs = std::max(c.gslabs, (P.mp + 63) / 64);
@@ -1245,7 +1269,8 @@ int solve_batched(int batch, const int* m, const int* n, int dtype, void* const*
       for (auto& c : cls) {
         for (int s = 0; s < c.max_steps; ++s)
           if (int r = launch_step(c.probs, c.count, c.km, c.max_half, c.gslabs, c.tslabs, 1, 1, s, fp32_only, true, pp,
-                                  ss, pr, nl))
+                                  ss, pr, nl, nullptr, nullptr,
+                                  o.fused_step == 1 && c.max_mp <= fused_step_max_rows(c.km)))
             return r;
         k_cache_step<<<c.count, 256, 0, ss>>>(c.probs, -2, -1);  // record the last step of the sweep
         k_sweep_reduce<<<c.count, 256, 0, ss>>>(c.probs, c.io, c.rec, 1, d_remaining);
@@ -1334,6 +1359,7 @@ void jacobi_default_opts(jac_opts* o) {
   o->want_v = 1;
   o->tol = 0.0;
   o->f64_products = JAC_F64_SPLIT16;
+  o->fused_step = 1;
 }
 
 const char* jacobi_status_string(int s) {

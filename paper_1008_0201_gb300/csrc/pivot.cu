@@ -222,21 +222,18 @@ __device__ float oz_residual(PivotSmem<KM, LPP>& sm, const double* Vs, int k, in
   return mloc;
 }
 
-// KM = 32: four CTAs per SM (shared memory allows four; the register cap keeps them resident, no
-// spills), which the batched solves of many small pivots need; KM = 64: one CTA per SM
-template <int KM, int LPP>
-__global__ void __launch_bounds__((KM / 2) * LPP, KM == 32 ? 4 : 1)
-    k_pivot(const JacProb* __restrict__ probs, int s, PivotParams pp) {
+// The pivot of one pair in one CTA.  Returns 0 when V_P was formed and the pair is to be updated,
+// 2 when the block was handed over to the FP64 pivot kernel (A_P still in sm.V), 1 otherwise (no
+// rotation, or a reported error); uniform over the CTA.  FUSED = false: A_P is read from the Gram kernel's output and
+// V_P written for the update kernel.  FUSED = true (the fused step kernel): A_P is already in
+// sm.V and V = I + W stays in shared memory (sm.Vf, sm.perm, sm.lpos) for the caller's update.
+template <int KM, int LPP, bool FUSED>
+__device__ __forceinline__ int pivot_block(PivotSmem<KM, LPP>& sm, const JacProb& a, int s, int pair,
+                                           const PivotParams& pp) {
   using SM = PivotSmem<KM, LPP>;
   constexpr int NT = SM::NT, NW = SM::NW;
   constexpr int LDF = SM::LDF, LDS = SM::LDS, LDV = SM::LDV;
-  extern __shared__ __align__(16) unsigned char pv_raw[];
-  SM& sm = *reinterpret_cast<SM*>(pv_raw);
-  const JacProb& a = probs[blockIdx.y];
   unsigned* err = a.pflags;
-  const int pair = blockIdx.x;
-  if (!a.active || s >= a.nsteps || pair >= a.counts[s]) return;
-  if (a.cached && a.cached[pair]) return;  // skip set, statistics kept (pair_cache.cu)
   PairStat* stats = a.stats + (size_t)s * a.half;
   const long long t_start = clock64();
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -250,12 +247,12 @@ __global__ void __launch_bounds__((KM / 2) * LPP, KM == 32 ? 4 : 1)
       atomicOr(err, JAC_DEVERR_INNER_LIMIT);
       a.skip[pair] = 1;
     }
-    return;
+    return 1;
   }
 
   // ---- 1. load A_P, scaled matrix E, statistics ----------------------------------------------
-  const double* A = a.Ap + (size_t)pair * a.apld * a.apld;
-  {
+  if constexpr (!FUSED) {
+    const double* A = a.Ap + (size_t)pair * a.apld * a.apld;
     // all of a thread's loads are issued before its stores: the global (L2) latency is paid
     // once, not once per element
     constexpr int NLD = (KM * KM + NT - 1) / NT;
@@ -303,7 +300,7 @@ __global__ void __launch_bounds__((KM / 2) * LPP, KM == 32 ? 4 : 1)
       st.evaluated = 1;
       stats[pair] = st;
     }
-    return;
+    return 1;
   }
   // off-diagonal e_ij = a_ij / (d_i d_j) in FP32: it is the scaled off-diagonal entry
   // |a_ij| / sqrt(a_ii a_jj) to FP32 accuracy, so it drives the statistics; only entries within
@@ -373,7 +370,7 @@ __global__ void __launch_bounds__((KM / 2) * LPP, KM == 32 ? 4 : 1)
       st.cyc[1] = st.cyc[2] = st.cyc[3] = 0;
       stats[pair] = st;
     }
-    return;
+    return 1;
   }
   __syncthreads();  // red_* and the trace slots are reused below
 
@@ -486,7 +483,7 @@ __global__ void __launch_bounds__((KM / 2) * LPP, KM == 32 ? 4 : 1)
       st.cyc[2] = st.cyc[3] = 0;
       stats[pair] = st;
     }
-    return;
+    return 2;
   }
   // R = Dp + F in pivot order: F[c][r] = (R~ - I)[r][c] d_c, r <= c; then d and the signs in
   // pivot order, and the logical order of the inner sweep
@@ -912,22 +909,24 @@ __global__ void __launch_bounds__((KM / 2) * LPP, KM == 32 ? 4 : 1)
       st.cyc[3] = t_ns - t_inner;
       stats[pair] = st;
     }
-    return;
+    return 2;
   }
   // V_P = P V Pi: V_P[perm[r]][l] = V[r][lpos[l]]
-  double* out = a.vp + (size_t)pair * a.apld * a.apld;
-  for (int e = tid; e < KP * KP; e += NT) {
-    const int r = e % KP, l = e / KP;
-    double v = 0.0;
-    int row = r;
-    if (r < k && l < k) {
-      v = Vs[sm.lpos[l] * LDV + r];
-      row = sm.perm[r];
+  if constexpr (!FUSED) {
+    double* out = a.vp + (size_t)pair * a.apld * a.apld;
+    for (int e = tid; e < KP * KP; e += NT) {
+      const int r = e % KP, l = e / KP;
+      double v = 0.0;
+      int row = r;
+      if (r < k && l < k) {
+        v = Vs[sm.lpos[l] * LDV + r];
+        row = sm.perm[r];
+      }
+      out[l * a.apld + row] = v;
     }
-    out[l * a.apld + row] = v;
   }
   if (tid == 0) {
-    a.skip[pair] = 0;
+    a.skip[pair] = FUSED ? 3 : 0;  // 3: updated by the fused step kernel itself
     st.rotations = total_rot;
     st.inner_sweeps = (inner < max_inner) ? inner + 1 : max_inner;
     st.ns_steps = ns;
@@ -937,12 +936,195 @@ __global__ void __launch_bounds__((KM / 2) * LPP, KM == 32 ? 4 : 1)
     st.cyc[3] = t_ns - t_inner;
     stats[pair] = st;
   }
+  return 0;
+}
+
+// KM = 32: four CTAs per SM (shared memory allows four; the register cap keeps them resident, no
+// spills), which the batched solves of many small pivots need; KM = 64: one CTA per SM
+template <int KM, int LPP>
+__global__ void __launch_bounds__((KM / 2) * LPP, KM == 32 ? 4 : 1)
+    k_pivot(const JacProb* __restrict__ probs, int s, PivotParams pp) {
+  extern __shared__ __align__(16) unsigned char pv_raw[];
+  PivotSmem<KM, LPP>& sm = *reinterpret_cast<PivotSmem<KM, LPP>*>(pv_raw);
+  const JacProb& a = probs[blockIdx.y];
+  const int pair = blockIdx.x;
+  if (!a.active || s >= a.nsteps || pair >= a.counts[s]) return;
+  if (a.cached && a.cached[pair]) return;  // skip set, statistics kept (pair_cache.cu)
+  pivot_block<KM, LPP, false>(sm, a, s, pair, pp);
+}
+
+// ---- the fused step kernel ---------------------------------------------------------------------
+// One step of the FP32 sweeps for one pair in one CTA: the Gram block, the pivot and the block
+// update, with X_P = [G_p G_q] read from global memory once and written once.  The m rows of X_P
+// stay in shared memory from the Gram to the update, in the pivot's digit-product region (the
+// FP32 sweeps never form the FP64 J-orthogonality residual); the rows of V go through the column
+// mailboxes in chunks of 64.  Used when every problem of the launch has m <= FusedLayout::MF.
+template <int KM, int LPP>
+struct FusedLayout {
+  using SM = PivotSmem<KM, LPP>;
+  static constexpr int LDX = KM + 4;  // staged rows of X_P (floats; 16-byte aligned rows)
+  static constexpr int LDB = KM + 4;  // V_P in FP32, row c = input column
+  static constexpr int REGION = (int)((sizeof(SM::M) > sizeof(SM::D) ? sizeof(SM::M) : sizeof(SM::D)) / 4);
+  static constexpr int MF = ((REGION - KM * LDB) / LDX) / 32 * 32;  // largest m
+  static_assert(MF >= 32, "staging region");
+  static_assert(2 * SM::P2 * SM::MBS >= 64 * LDX, "a 64-row chunk of V fits in the mailboxes");
+};
+
+template <int KM, int LPP>
+__global__ void __launch_bounds__((KM / 2) * LPP, KM == 32 ? 4 : 1)
+    k_step_fused(const JacProb* __restrict__ probs, int s, PivotParams pp) {
+  using SM = PivotSmem<KM, LPP>;
+  using FL = FusedLayout<KM, LPP>;
+  constexpr int NT = SM::NT, LDS = SM::LDS, LDV = SM::LDV, LDX = FL::LDX, LDB = FL::LDB, MF = FL::MF;
+  constexpr int CT = KM / 4;  // 4-column groups
+  static_assert(NT % CT == 0 && NT / CT == 16, "16 row groups");
+  extern __shared__ __align__(16) unsigned char pv_raw[];
+  SM& sm = *reinterpret_cast<SM*>(pv_raw);
+  const JacProb& a = probs[blockIdx.y];
+  const int pair = blockIdx.x;
+  if (!a.active || s >= a.nsteps || pair >= a.counts[s]) return;
+  if (a.cached && a.cached[pair]) return;  // skip set, statistics kept (pair_cache.cu)
+  const int tid = threadIdx.x, tx = tid % CT, ty = tid / CT;
+  const int* sp = a.pairs + (size_t)s * a.half * 2;
+  const int p = sp[2 * pair], q = sp[2 * pair + 1];
+  const int op = a.boff[p], wp = a.boff[p + 1] - op, oq = a.boff[q], wq = a.boff[q + 1] - oq;
+  const int k = wp + wq, m = a.mp;
+  // the driver launches this kernel for the FP32 sweeps (no FP64 residual: the staging region is
+  // free) within these bounds; anything else is reported, never trapped
+  if (k > KM || m > MF || pp.ns_mode) {
+    if (tid == 0) {
+      atomicOr(a.pflags, JAC_DEVERR_INNER_LIMIT);
+      a.skip[pair] = 1;
+    }
+    return;
+  }
+  auto pcol = [&](int c) { return c < wp ? op + c : oq + (c - wp); };
+  float* Xs = reinterpret_cast<float*>(&sm.M[0]);  // [r][c], m rows
+  float* Bs = Xs + MF * LDX;                       // [c][j]
+  float* Vst = &sm.mb[0][0];                       // 64-row chunk of V, [r][c]
+
+  // ---- 0. X_P into shared memory; A_P = X_P^T X_P in FP32 (FP64 storage for the pivot)
+  {
+    constexpr int NB = 16;  // loads in flight per thread
+    for (int e0 = 0; e0 < k * m; e0 += NT * NB) {
+      float v[NB];
+#pragma unroll
+      for (int u = 0; u < NB; ++u) {
+        const int e = e0 + u * NT + tid;  // consecutive threads: consecutive rows of a column
+        v[u] = (e < k * m) ? __ldg(a.G32 + (size_t)pcol(e / m) * a.mp + e % m) : 0.0f;
+      }
+#pragma unroll
+      for (int u = 0; u < NB; ++u) {
+        const int e = e0 + u * NT + tid;
+        if (e < k * m) Xs[(e % m) * LDX + e / m] = v[u];
+      }
+    }
+  }
+  __syncthreads();
+  {
+    // thread (ty, tx): rows RPT ty .. RPT ty + RPT - 1 and columns 4 tx .. 4 tx + 3 of A_P; the
+    // entries (i, j) and (j, i) take the same products in the same order (exactly symmetric)
+    constexpr int RPT = KM / 16;
+    float acc[RPT][4];
+#pragma unroll
+    for (int u = 0; u < RPT; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[u][v] = 0.0f;
+    for (int r = 0; r < m; ++r) {
+      const float* xr = Xs + r * LDX;
+      const float4 xj = *reinterpret_cast<const float4*>(xr + 4 * tx);
+      const float vj[4] = {xj.x, xj.y, xj.z, xj.w};
+#pragma unroll
+      for (int u = 0; u < RPT; ++u) {
+        const float xi = xr[RPT * ty + u];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(xi, vj[v], acc[u][v]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < RPT; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const int i = RPT * ty + u, j = 4 * tx + v;
+        if (i < k && j < k) sm.V[j * LDV + i] = oz_f2d(acc[u][v]);
+      }
+  }
+  // (pivot_block's first barrier publishes A_P)
+
+  // ---- 1.-4. the pivot
+  const int pr = pivot_block<KM, LPP, true>(sm, a, s, pair, pp);  // uniform
+  if (pr == 2) {
+    // handed over: the FP64 pivot kernel reads A_P from the Gram output, as after the Gram kernel
+    double* A = a.Ap + (size_t)pair * a.apld * a.apld;
+    for (int e = tid; e < k * k; e += NT) A[(e / k) * a.apld + e % k] = sm.V[(e / k) * LDV + e % k];
+  }
+  if (pr != 0) return;
+
+  // ---- 5. [X_P; V rows] <- [X_P; V rows] V_P in FP32, V_P[perm[r]][l] = V[r][lpos[l]]
+  __syncthreads();
+  for (int e = tid; e < k * k; e += NT) {
+    const int r = e % k, l = e / k;
+    Bs[sm.perm[r] * LDB + l] = sm.Vf[sm.lpos[l] * LDS + r];
+  }
+  __syncthreads();
+  // thread (ty, tx): rows 4 ty .. 4 ty + 3 of a 64-row chunk, columns 4 tx .. 4 tx + 3
+  auto update_chunk = [&](const float* X, int rows, float* dst, int ld, int r0) {
+    float acc[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[u][v] = 0.0f;
+    for (int c = 0; c < k; ++c) {
+      const float4 b = *reinterpret_cast<const float4*>(Bs + c * LDB + 4 * tx);
+      const float bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float x = X[(4 * ty + u) * LDX + c];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(x, bv[v], acc[u][v]);
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int j = 4 * tx + v;
+      if (j >= k) continue;
+      float* col = dst + (size_t)pcol(j) * ld + r0;
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (4 * ty + u < rows) col[4 * ty + u] = acc[u][v];
+    }
+  };
+  for (int r0 = 0; r0 < m; r0 += 64) update_chunk(Xs + r0 * LDX, min(64, m - r0), a.G32, a.mp, r0);
+  if (a.V32) {
+    for (int r0 = 0; r0 < a.np; r0 += 64) {
+      const int rows = min(64, a.np - r0);
+      constexpr int NV = KM * 64 / NT;
+      float v[NV];
+#pragma unroll
+      for (int u = 0; u < NV; ++u) {
+        const int e = u * NT + tid, c = e / 64, r = e % 64;
+        v[u] = (c < k && r < rows) ? a.V32[(size_t)pcol(c) * a.np + r0 + r] : 0.0f;
+      }
+      __syncthreads();  // the previous chunk's reads of Vst are done
+#pragma unroll
+      for (int u = 0; u < NV; ++u) {
+        const int e = u * NT + tid;
+        Vst[(e % 64) * LDX + e / 64] = v[u];
+      }
+      __syncthreads();
+      update_chunk(Vst, rows, a.V32, a.np, r0);
+    }
+  }
 }
 
 // Lanes per pair slot of each pivot capacity: KM = 64 -> 8 lanes x 8 rows, 256 threads;
 // KM = 32 -> 8 lanes x 4 rows, 128 threads.
 constexpr int kLpp64 = 8, kLpp32 = 8;
 static_assert(sizeof(PivotSmem<64, kLpp64>) <= 232448, "pivot shared memory above the 227 KB per-CTA limit");
+
+int fused_step_max_rows(int km) {
+  return km == 32 ? FusedLayout<32, kLpp32>::MF : FusedLayout<64, kLpp64>::MF;
+}
 
 size_t pivot_smem_bytes(int km) {
   return km == 32 ? sizeof(PivotSmem<32, kLpp32>) : sizeof(PivotSmem<64, kLpp64>);
@@ -953,6 +1135,10 @@ int pivot_set_attributes() {
   bool ok = cudaFuncSetAttribute(k_pivot<32, kLpp32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)sizeof(PivotSmem<32, kLpp32>)) == cudaSuccess;
   ok &= cudaFuncSetAttribute(k_pivot<64, kLpp64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(PivotSmem<64, kLpp64>)) == cudaSuccess;
+  ok &= cudaFuncSetAttribute(k_step_fused<32, kLpp32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(PivotSmem<32, kLpp32>)) == cudaSuccess;
+  ok &= cudaFuncSetAttribute(k_step_fused<64, kLpp64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sizeof(PivotSmem<64, kLpp64>)) == cudaSuccess;
   return ok ? 0 : 1;
 }
@@ -966,6 +1152,17 @@ void pivot_launch(int km, int max_half, int nprob, cudaStream_t st, const JacPro
   else
     k_pivot<64, kLpp64><<<dim3(max_half, nprob), PivotSmem<64, kLpp64>::NT, sizeof(PivotSmem<64, kLpp64>), st>>>(
         probs, s, pp);
+}
+
+// Grid (max_half, nprob): one CTA per pair, the whole FP32 step (fused_step_max_rows bounds m).
+void fused_step_launch(int km, int max_half, int nprob, cudaStream_t st, const JacProb* probs, int s,
+                       const PivotParams& pp) {
+  if (km == 32)
+    k_step_fused<32, kLpp32><<<dim3(max_half, nprob), PivotSmem<32, kLpp32>::NT, sizeof(PivotSmem<32, kLpp32>),
+                               st>>>(probs, s, pp);
+  else
+    k_step_fused<64, kLpp64><<<dim3(max_half, nprob), PivotSmem<64, kLpp64>::NT, sizeof(PivotSmem<64, kLpp64>),
+                               st>>>(probs, s, pp);
 }
 
 }  // namespace jac
