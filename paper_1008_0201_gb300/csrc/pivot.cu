@@ -597,14 +597,21 @@ __device__ __forceinline__ int pivot_block(PivotSmem<KM, LPP>& sm, const JacProb
         const bool trig = sm.jphys[ii] == sm.jphys[jj];
         const float aii = fmaf(si, si, cni), ajj = fmaf(sj, sj, cnj);
         const float rs = rsqrtf(aii) * rsqrtf(ajj);
-        float sij = 0.0f;
+        // a_ij = (d_i e_i + f_i) . (d_j e_j + f_j) = s_i F_ij + s_j F_ji + f_i . f_j in one group
+        // reduction: the cross terms enter the partial sums of the lanes that hold rows i and j
+        // (predicated FMAs; fetching F_ij and F_ji from the owner lanes first costs a dependent
+        // select chain and a shuffle per entry, ~11% of the step)
+        float sij = 0.0f, xc = 0.0f;
 #pragma unroll
-        for (int u = 0; u < R; ++u) sij = fmaf(fi[u], fj[u], sij);
-        sij = group_sum<LPP>(sij);
-        const float fji = col_entry<R>(fj, ii, lane0);  // F_ij: row i of column j
-        const float fij = col_entry<R>(fi, jj, lane0);  // F_ji
+        for (int u = 0; u < R; ++u) {
+          const int row = l * R + u;
+          sij = fmaf(fi[u], fj[u], sij);
+          if (row == ii) xc = fmaf(si, fj[u], xc);
+          if (row == jj) xc = fmaf(sj, fi[u], xc);
+        }
+        const float aij_all = group_sum<LPP>(sij + xc);
         if (act) {
-          const float aij = si * fji + sj * fij + sij;
+          const float aij = aij_all;
           const float beta = fabsf(aij);
           const float scaled = beta * rs;
           if (scaled > tol_in) {
@@ -971,7 +978,7 @@ struct FusedLayout {
 };
 
 template <int KM, int LPP>
-__global__ void __launch_bounds__((KM / 2) * LPP, KM == 32 ? 4 : 1)
+__global__ void __launch_bounds__((KM / 2) * LPP, KM == 32 ? 3 : 1)  // KM = 32: no spills at 3 per SM
     k_step_fused(const JacProb* __restrict__ probs, int s, PivotParams pp) {
   using SM = PivotSmem<KM, LPP>;
   using FL = FusedLayout<KM, LPP>;
