@@ -237,6 +237,22 @@ __device__ __forceinline__ int pivot_block(PivotSmem<KM, LPP>& sm, const JacProb
   PairStat* stats = a.stats + (size_t)s * a.half;
   const long long t_start = clock64();
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // ---- 1. load A_P, scaled matrix E, statistics ----------------------------------------------
+  // The A_P tile's address depends on the pair slot only: its loads (the whole KM x KM tile,
+  // entries beyond k unused) are issued first, so that their latency overlaps the dependent
+  // lookups of the pair's blocks below (pair table, block offsets: ~10k clocks per pivot when
+  // they ran in sequence on GB300)
+  constexpr int NLD = KM * KM / NT;
+  static_assert(NLD * NT == KM * KM, "whole tile per thread set");
+  double av[NLD];
+  if constexpr (!FUSED) {
+    const double* A = a.Ap + (size_t)pair * a.apld * a.apld;
+#pragma unroll
+    for (int u = 0; u < NLD; ++u) {
+      const int e = tid + u * NT;
+      av[u] = __ldg(A + (e / KM) * a.apld + e % KM);
+    }
+  }
   const int* sp = a.pairs + (size_t)s * a.half * 2;
   const int p = sp[2 * pair], q = sp[2 * pair + 1];
   const int op = a.boff[p], wp = a.boff[p + 1] - op, oq = a.boff[q], wq = a.boff[q + 1] - oq;
@@ -249,31 +265,20 @@ __device__ __forceinline__ int pivot_block(PivotSmem<KM, LPP>& sm, const JacProb
     }
     return 1;
   }
-
-  // ---- 1. load A_P, scaled matrix E, statistics ----------------------------------------------
+  // the sign of this thread's column, needed after the first barrier
+  const int jcol = (tid < k) ? a.Js[tid < wp ? op + tid : oq + (tid - wp)] : 0;
   if constexpr (!FUSED) {
-    const double* A = a.Ap + (size_t)pair * a.apld * a.apld;
-    // all of a thread's loads are issued before its stores: the global (L2) latency is paid
-    // once, not once per element
-    constexpr int NLD = (KM * KM + NT - 1) / NT;
-    double v[NLD];
 #pragma unroll
     for (int u = 0; u < NLD; ++u) {
-      const int e = tid + u * NT;
-      v[u] = (e < k * k) ? __ldg(A + (e / k) * a.apld + e % k) : 0.0;
-    }
-#pragma unroll
-    for (int u = 0; u < NLD; ++u) {
-      const int e = tid + u * NT;
-      if (e < k * k) Vs[(e / k) * LDV + e % k] = v[u];
+      const int e = tid + u * NT, r = e % KM, c = e / KM;
+      if (r < k && c < k) Vs[c * LDV + r] = av[u];
     }
   }
   if (tid == 0) sm.bad = 0;
   __syncthreads();
   double tr = 0.0;
   if (tid < k) {
-    const int col = tid < wp ? op + tid : oq + (tid - wp);
-    sm.jloc[tid] = a.Js[col];
+    sm.jloc[tid] = jcol;
     const double aii = Vs[tid * LDV + tid];
     if (!(aii > 0.0) || !(aii < 1.0e300)) atomicOr(&sm.bad, 1);
     const float d = sqrtf((float)aii);
@@ -309,9 +314,12 @@ __device__ __forceinline__ int pivot_block(PivotSmem<KM, LPP>& sm, const JacProb
   const float tolf = (float)tol;
   float mx = 0.0f, oc = 0.0f, od = 0.0f;
   int cnt = 0;
-  for (int e = tid; e < k * k; e += NT) {
-    const int i = e % k, j = e / k;
-    if (i == j) continue;
+  // the whole KM x KM tile in a fixed, unrolled pattern (no division by k; the loads of the
+  // iterations issue together), entries beyond k skipped
+#pragma unroll
+  for (int u = 0; u < NLD; ++u) {
+    const int e = tid + u * NT, i = e % KM, j = e / KM;
+    if (i >= k || j >= k || i == j) continue;
     const float aij = (float)Vs[j * LDV + i];
     const float eij = aij * sm.fid[i] * sm.fid[j];
     sm.S[j * LDS + i] = eij;
