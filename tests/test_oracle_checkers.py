@@ -1,6 +1,6 @@
 """Pins of the oracle's wide-precision checkers against exact rational arithmetic (-m "not gpu").
 
-Every GPU parity verdict on the off-norm, the J-unitarity of V and the factor residual comes
+Every GPU parity decision on the off-norm, the J-unitarity of V and the factor residual comes
 from oracle_check_offdiag, oracle_check_vjv and oracle_check_factor_residual.  These tests feed
 them matrices with known NONZERO answers -- small integer (and Gaussian-integer) matrices whose
 Gram entries, V^* J V - J and G0 V - G are exact rationals -- and compare with a plain
