@@ -44,7 +44,7 @@ def test_hsvd_argument_positions(lib, dtype):
     assert _hsvd(lib, dtype=dtype, J=None) == -6
     for bad in (dict(block_w=0), dict(block_w=33), dict(ordering=4), dict(block_mode=2), dict(factor=3),
                 dict(precision=3), dict(max_sweeps=0), dict(want_v=2), dict(f64_products=3),
-                dict(f64_products=-1)):
+                dict(f64_products=-1), dict(fused_step=2), dict(fused_step=-1)):
         assert _hsvd(lib, dtype=dtype, opts=_opts(**bad)) == -7, bad
     assert _hsvd(lib, dtype=dtype, lam=None) == -8
     assert _hsvd(lib, dtype=dtype, U=FAKE2, ldu=3) == -10
@@ -108,6 +108,7 @@ def test_batched_argument_positions(lib):
     assert _batched(lib, opts=_opts(ordering=3)) == -8  # per-cycle weight ordering: single solves only
     assert _batched(lib, opts=_opts(precision=1)) == -8  # the mixed mode: single solves only
     assert _batched(lib, opts=_opts(f64_products=3)) == -8
+    assert _batched(lib, opts=_opts(fused_step=2)) == -8
     assert _batched(lib, drop=("lam",)) == -9
     assert _batched(lib, U=(0x700000, 0x800000)) == -11  # U without ldu
     assert _batched(lib, drop=("V",)) == -12
