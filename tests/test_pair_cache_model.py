@@ -97,3 +97,46 @@ def test_cache_takes_the_same_decisions(ordering, nb):
     # once nothing rotates for a whole sweep, the next sweep evaluates nothing at all
     last = [d for d in got if d[0] == len(tols) - 1]
     assert not any(d[3] for d in last)
+
+
+# ---- the skip codes of one step with the fused FP32 step kernel (csrc/pivot.cu, capi.cu) ----
+# per pair: 1 = no rotation (or a reported error), 2 = handed over to the FP64 pivot kernel,
+# 0 = V_P formed for the separate update kernel, 3 = updated by the fused kernel itself.  The
+# FP64 pivot kernel acts on 2 only (turning it into 0 on success, 1 on a singular block); the
+# plain update acts on 0 only; the pair cache counts every code but 1 as a rotation.
+
+def step_codes(outcomes, fused, fallback, fp64_ok):
+    """outcomes[i] in {'none', 'rotate', 'handover'}: the FP32 pivot's result for pair i.
+    Returns (updates applied per pair, final codes)."""
+    code = [1 if o == "none" else (2 if o == "handover" else (3 if fused else 0)) for o in outcomes]
+    applied = [1 if (fused and c == 3) else 0 for c in code]  # the fused kernel's own update
+    if fallback:
+        for i, c in enumerate(code):
+            if c == 2:
+                code[i] = 0 if fp64_ok[i] else 1
+    for i, c in enumerate(code):  # the plain update kernel
+        if c == 0:
+            applied[i] += 1
+    return applied, code
+
+
+@pytest.mark.parametrize("fused", [False, True])
+@pytest.mark.parametrize("fallback", [False, True])
+def test_fused_step_updates_each_pair_once(fused, fallback):
+    import itertools
+
+    kinds = ("none", "rotate", "handover")
+    for outcomes in itertools.product(kinds, repeat=3):
+        for fp64_ok in itertools.product((False, True), repeat=3):
+            applied, code = step_codes(list(outcomes), fused, fallback, fp64_ok)
+            for o, a, c, ok in zip(outcomes, applied, code, fp64_ok):
+                if o == "rotate":
+                    assert a == 1  # exactly once, by whichever kernel owns the pair
+                elif o == "none":
+                    assert a == 0 and c == 1
+                else:  # handed over: rotated once by the FP64 path, or left for a later sweep
+                    assert a == (1 if (fallback and ok) else 0)
+                # the pair cache treats the pair as unchanged exactly when nothing was applied,
+                # except a handover left unrotated (code 2), which it must re-evaluate
+                rotated_for_cache = c != 1
+                assert rotated_for_cache == (a == 1 or (o == "handover" and not fallback))
